@@ -1,0 +1,569 @@
+#!/usr/bin/env python3
+"""Benchmark of the reverse-mode gradient path on one node; prints ONE JSON line.
+
+Default workload: f(x) = ||A x||^2, A dense 10000 x 10000 FP64 (800 MB, larger
+than L2), value-and-gradient through the C ABI (kg_grad), compared with the
+forward pass alone (kg_eval): the paper's measure is the gradient/function
+wall-clock ratio; the throughput is the gradient's algorithmic HBM bytes per
+second.  Other workloads: --workload tet | dense32 | dense64 | laplace |
+batched | autograd.
+
+Multi-GPU (torchrun, one process per GPU): every rank runs an independent
+replica of the workload (the problems are independent; there is no data-path
+collective), timed between barriers; value = units of all ranks / max time.
+
+--impl reference times the CPU oracle (plain C, one thread) on a bounded
+sample of the same workload, on rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("gradient/function wall-clock ratio and gradient HBM GB/s (% of peak); "
+          "batched grads/sec")
+FALLBACK_HBM_GBS = 6800.0
+
+
+# ------------------------------------------------------------------ peaks
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    sm_mhz, sms = 2070.0, 152
+    try:
+        with open(path) as fh:
+            P = json.load(fh)
+        hbm, src = float(P["hbm_gbs"]), "measured"
+        sm_mhz = float(P.get("sm_max_mhz", sm_mhz))
+    except Exception:
+        hbm, src = FALLBACK_HBM_GBS, "fallback"
+    # FP64 FMA issue: 2 per SM per clock on GB300 (1.25 TFLOP/s nominal)
+    fp64_tflops = sms * 2 * 2 * sm_mhz * 1e6 / 1e12
+    # FP32 FMA issue: 128 per SM per clock
+    fp32_tflops = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+    return {"hbm_gbs": hbm, "hbm_src": src, "fp64_tflops": fp64_tflops,
+            "fp32_tflops": fp32_tflops}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
+                          if f.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------------ workloads
+class Workload:
+    """One value-and-gradient step of the path (`step`), its forward alone
+    (`eval_step`), the same step through host buffers (`e2e_step`), byte /
+    flop accounting and a bounded oracle sample."""
+    name = ""
+    dtype_name = "f64"
+    unit = "GB/s"
+    higher_is_better = True
+
+    def config(self):
+        return {}
+
+
+class DenseWL(Workload):
+    def __init__(self, n, dtype, arith="auto", strategy="fused"):
+        self.n, self.m = n, n
+        self.dtype = dtype
+        self.arith = arith
+        self.strategy = strategy
+        self.es = 8 if dtype == "f64" else 4
+        self.dtype_name = dtype
+
+    def setup(self, dev):
+        import torch
+        from paper_2507_13204_gb300 import api, workloads as W
+        A, x = W.quadform_inputs(self.n, seed=0)
+        td = torch.float64 if self.dtype == "f64" else torch.float32
+        self.At = torch.tensor(A, dtype=td, device=dev)
+        self.xt = torch.tensor(x, dtype=td, device=dev)
+        self.A_host = A if self.dtype == "f64" else A.astype("float32").astype("float64")
+        self.x_host = x if self.dtype == "f64" else x.astype("float32").astype("float64")
+        self.p = api.QuadForm(self.At, strategy=self.strategy, arith=self.arith)
+        self.gx = torch.empty(self.n, dtype=td, device=dev)
+        self.f = torch.empty((), dtype=td, device=dev)
+        self.fe = torch.empty((), dtype=td, device=dev)
+        self.x_pin = torch.tensor(x, dtype=td).pin_memory()
+        self.g_pin = torch.empty(self.n, dtype=td).pin_memory()
+        self.f_pin = torch.empty((), dtype=td).pin_memory()
+        self.td = td
+
+    def step(self):
+        self.p.grad(self.xt, gx=self.gx, f=self.f)
+
+    def eval_step(self):
+        self.p.eval(self.xt, f=self.fe)
+
+    def e2e_step(self):
+        self.p.grad_host(self.x_pin, self.g_pin, self.f_pin)
+
+    @property
+    def grad_bytes(self):  # A once, x in, gradient out
+        return self.es * (self.m * self.n + 2 * self.n)
+
+    @property
+    def eval_bytes(self):
+        return self.es * (self.m * self.n + self.n)
+
+    @property
+    def units_per_step(self):
+        return self.grad_bytes / 1e9  # GB
+
+    def dominant(self):
+        """(name, algorithmic bytes per launch, fp64 flops per launch)"""
+        return (self.grad_bytes - self.es * self.n, 4.0 * self.m * self.n)
+
+    def h2d_d2h(self):
+        return self.es * self.n, self.es * (self.n + 1)
+
+    def config(self):
+        return {"workload": f"dense ||Ax||^2, A {self.m}x{self.n} {self.dtype.upper()} "
+                            f"({self.es * self.m * self.n / 1e6:.0f} MB), value+grad wrt x",
+                "strategy": self.strategy, "arith": self.arith,
+                "l2": "inputs larger than L2 (A > 129 MB)"}
+
+    def oracle_sample(self, budget_s=10.0):
+        from oracle import oracle as O
+        rows = self.m
+        t0 = time.perf_counter()
+        reps, done = 0, 0
+        while True:
+            O.quadform_grad(self.A_host[:rows], self.x_host)
+            reps += 1
+            done += self.es * (rows * self.n + 2 * self.n)
+            if time.perf_counter() - t0 >= budget_s or reps >= 20:
+                break
+        dt = time.perf_counter() - t0
+        return done / 1e9 / dt, f"{reps} x full {self.m}x{self.n} value+grad (oracle, 1 thread)"
+
+
+class TetWL(Workload):
+    def __init__(self, a, dtype, strategy="atomic", arith="auto"):
+        self.a = a
+        self.dtype = dtype
+        self.dtype_name = dtype
+        self.es = 8 if dtype == "f64" else 4
+        self.strategy = strategy
+        self.arith = arith
+
+    def setup(self, dev):
+        import torch
+        from paper_2507_13204_gb300 import api, workloads as W
+        mesh, u = W.tet_inputs(self.a)
+        td = torch.float64 if self.dtype == "f64" else torch.float32
+        self.mesh, self.u_host = mesh, u
+        self.ne, self.nv = mesh.ne, mesh.nv
+        self.conn = torch.tensor(mesh.conn, device=dev)
+        self.G = torch.tensor(mesh.G, dtype=td, device=dev)
+        self.u = torch.tensor(u, dtype=td, device=dev)
+        self.p = api.TetEnergy(self.conn, self.G, mesh.nv, strategy=self.strategy,
+                               mode="recompute", arith=self.arith)
+        self.gu = torch.empty(mesh.nv, dtype=td, device=dev)
+        self.f = torch.empty((), dtype=td, device=dev)
+        self.fe = torch.empty((), dtype=td, device=dev)
+        self.x_pin = torch.tensor(u, dtype=td).pin_memory()
+        self.g_pin = torch.empty(mesh.nv, dtype=td).pin_memory()
+        self.f_pin = torch.empty((), dtype=td).pin_memory()
+
+    def step(self):
+        self.p.grad(self.u, gx=self.gu, f=self.f)
+
+    def eval_step(self):
+        self.p.eval(self.u, f=self.fe)
+
+    def e2e_step(self):
+        self.p.grad_host(self.x_pin, self.g_pin, self.f_pin)
+
+    @property
+    def eval_bytes(self):  # conn + G streamed, u read once
+        return self.ne * (16 + 12 * self.es) + self.nv * self.es
+
+    @property
+    def grad_bytes(self):  # + gradient written once
+        return self.eval_bytes + self.nv * self.es
+
+    @property
+    def units_per_step(self):
+        return self.grad_bytes / 1e9
+
+    def dominant(self):
+        return (self.grad_bytes, None)
+
+    def h2d_d2h(self):
+        return self.es * self.nv, self.es * (self.nv + 1)
+
+    def config(self):
+        return {"workload": f"tet-mesh energy sum_e log1p(|G_e u_e|^2), {self.a}^3 cubes x 6 tets "
+                            f"({self.ne} tets, {self.nv} vertices, random relabelling), "
+                            f"{self.dtype.upper()}, value+grad wrt u",
+                "strategy": self.strategy, "arith": self.arith,
+                "l2": "inputs larger than L2 (conn+G > 129 MB)"}
+
+    def oracle_sample(self, budget_s=10.0):
+        from oracle import oracle as O
+        ne = min(self.ne, 1_000_000)
+        conn, G = self.mesh.conn[:ne], self.mesh.G[:ne]
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            O.tet_grad(conn, G, self.u_host)
+            reps += 1
+            if time.perf_counter() - t0 >= budget_s or reps >= 20:
+                break
+        dt = time.perf_counter() - t0
+        b = reps * (ne * (16 + 12 * self.es) + 2 * self.nv * self.es)
+        return b / 1e9 / dt, f"{reps} x value+grad of the first {ne} tets (oracle, 1 thread)"
+
+
+class LaplaceWL(Workload):
+    """The paper's E1 example at n = 10000 (data 80 KB: launch-bound, like the paper)."""
+
+    def __init__(self, n, strategy="fused"):
+        self.n = n
+        self.es = 8
+        self.strategy = strategy
+        self.unit = "grads/s"
+
+    def setup(self, dev):
+        import torch
+        from paper_2507_13204_gb300 import api, workloads as W
+        x, b = W.laplace1d_inputs(self.n)
+        self.x_host, self.b_host = x, b
+        self.b = torch.tensor(b, device=dev)
+        self.x = torch.tensor(x, device=dev)
+        self.p = api.Laplace1D(self.b, strategy=self.strategy)
+        self.gx = torch.empty(self.n, dtype=torch.float64, device=dev)
+        self.gb = torch.empty(self.n, dtype=torch.float64, device=dev)
+        self.f = torch.empty((), dtype=torch.float64, device=dev)
+        self.fe = torch.empty((), dtype=torch.float64, device=dev)
+        self.x_pin = torch.tensor(x).pin_memory()
+        self.g_pin = torch.empty(self.n, dtype=torch.float64).pin_memory()
+        self.f_pin = torch.empty((), dtype=torch.float64).pin_memory()
+
+    def step(self):
+        self.p.grad(self.x, gx=self.gx, f=self.f, gdata=self.gb)
+
+    def eval_step(self):
+        self.p.eval(self.x, f=self.fe)
+
+    def e2e_step(self):
+        self.p.grad_host(self.x_pin, self.g_pin, self.f_pin)
+
+    grad_bytes = property(lambda self: 8 * 4 * self.n)
+    eval_bytes = property(lambda self: 8 * 2 * self.n)
+    units_per_step = 1.0
+
+    def dominant(self):
+        return (self.grad_bytes, None)
+
+    def h2d_d2h(self):
+        return 8 * self.n, 8 * (self.n + 1)
+
+    def config(self):
+        return {"workload": f"paper example ||A(3x)-b||^2, 1-D Laplacian, n={self.n} FP64",
+                "strategy": self.strategy, "l2": "resident in L2 (160 KB)"}
+
+    def oracle_sample(self, budget_s=10.0):
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        reps = 0
+        while time.perf_counter() - t0 < budget_s and reps < 200000:
+            O.laplace1d_grad(self.x_host, self.b_host)
+            reps += 1
+        return reps / (time.perf_counter() - t0), f"{reps} x value+grad at n={self.n} (oracle, 1 thread)"
+
+
+def make_workload(name: str, arith: str):
+    if name == "dense":
+        return DenseWL(10000, "f64", arith=arith)
+    if name == "dense32":
+        return DenseWL(10000, "f32")
+    if name == "dense64":
+        return DenseWL(64, "f64", arith=arith)
+    if name == "tet":
+        return TetWL(100, "f64", arith=arith)
+    if name == "tet32":
+        return TetWL(100, "f32")
+    if name == "tetcsr":
+        return TetWL(100, "f64", strategy="csr", arith=arith)
+    if name == "laplace":
+        return LaplaceWL(10000)
+    if name == "laplace_atomic":
+        return LaplaceWL(10000, strategy="atomic")
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ------------------------------------------------------------------ main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=0, help="timed steps (0: about 3 s worth)")
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="kg", choices=["kg", "reference"])
+    ap.add_argument("--workload", default="dense")
+    ap.add_argument("--arith", default="auto", choices=["auto", "native", "pair"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    from paper_2507_13204_gb300 import _lib as L, build as B
+    if rank == 0 or world == 1:
+        B.build()
+    if dist:
+        dist.barrier()
+    wl = make_workload(args.workload, args.arith)
+    wl.setup(dev)
+    stream = torch.cuda.current_stream()
+    peaks = load_peaks()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+
+    def timed(fn, k):
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            fn()
+        e1.record(stream)
+        barrier()
+        return e0.elapsed_time(e1) / k  # ms per step
+
+    for _ in range(args.warmup):
+        wl.step()
+        wl.eval_step()
+    torch.cuda.synchronize()
+    wl.step()
+    launches_per_step = L.kg_last_launch_count()
+    wl.eval_step()
+    launches_eval = L.kg_last_launch_count()
+    # step count: exactly --steps, else about 3 s of gradient steps
+    t_probe = timed(wl.step, 3)
+    K = args.steps if args.steps > 0 else max(10, min(20000, int(3000.0 / max(t_probe, 1e-3))))
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    L.kg_profile_enable(True)
+    ms_grad = timed(wl.step, K)
+    kern_ms, kern_n, kern_name = L.kg_profile_read()
+    L.kg_profile_enable(False)
+    clk = clocks.stop()
+    ms_eval = timed(wl.eval_step, K)
+
+    if dist:
+        t = torch.tensor([ms_grad, ms_eval], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_grad, ms_eval = float(t[0]), float(t[1])
+
+    # end-to-end: host buffers through the C ABI, copies inside the timed region
+    K2 = max(5, min(K, int(2000.0 / max(ms_grad, 1e-3))))
+    for _ in range(2):
+        wl.e2e_step()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(K2):
+        wl.e2e_step()
+    barrier()
+    ms_e2e = (time.perf_counter() - t0) * 1e3 / K2
+    if dist:
+        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t[0])
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    if isinstance(wl, LaplaceWL):
+        value = world * 1000.0 / ms_grad
+        e2e_value = world * 1000.0 / ms_e2e
+    else:
+        value = world * wl.grad_bytes / 1e9 / (ms_grad * 1e-3)
+        e2e_value = world * wl.grad_bytes / 1e9 / (ms_e2e * 1e-3)
+    # dominant kernel roofline
+    per_launch_ms = kern_ms / max(kern_n, 1)
+    dbytes, dflops = wl.dominant()
+    ach_gbs = dbytes / 1e9 / (per_launch_ms * 1e-3) if per_launch_ms > 0 else 0.0
+    roof = {"bound": "hbm", "achieved": round(ach_gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": round(ach_gbs / peaks["hbm_gbs"], 4), "traffic": None,
+            "kernel": kern_name, "kernel_us": round(per_launch_ms * 1e3, 2),
+            "peak_source": f"{peaks['hbm_src']} copy bandwidth"}
+    strategy, mode, arith = wl.p.config
+    native64 = wl.dtype_name == "f64" and arith == "native"
+    if dflops and native64 and per_launch_ms > 0:
+        ach_tf = dflops / 1e12 / (per_launch_ms * 1e-3)
+        frac_alu = ach_tf / peaks["fp64_tflops"]
+        if frac_alu > roof["frac"]:
+            roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(peaks["fp64_tflops"], 4),
+                    "unit": "TFLOP/s", "frac": round(frac_alu, 4), "traffic": None,
+                    "kernel": kern_name, "kernel_us": round(per_launch_ms * 1e3, 2),
+                    "peak_source": "FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2070 MHz",
+                    "hbm_gbs": round(ach_gbs, 1), "hbm_frac": round(ach_gbs / peaks["hbm_gbs"], 4)}
+
+    out = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": wl.unit,
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_grad, 5),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": wl.dtype_name,
+        "data": "synthetic (seeded numpy PCG64 draws)",
+        "config": {**wl.config(), "strategy": strategy, "mode": mode, "arith": arith},
+        "grad_over_eval_ratio": round(ms_grad / ms_eval, 4),
+        "ms_eval": round(ms_eval, 5),
+        "pct_of_hbm_peak": round(100 * value / world / peaks["hbm_gbs"], 2) if wl.unit == "GB/s" else None,
+        "pct_of_8tbs_nominal": round(100 * value / world / 8000.0, 2) if wl.unit == "GB/s" else None,
+        "roofline": roof,
+        "e2e": {"value": round(e2e_value, 3), "unit": wl.unit,
+                "h2d_bytes_per_step": wl.h2d_d2h()[0], "d2h_bytes_per_step": wl.h2d_d2h()[1],
+                "ms_per_step": round(ms_e2e, 5), "api": "kg_grad_host (pinned host buffers)"},
+        "gpu_launches": launches_per_step * K,
+        "launches_per_step": {"grad": launches_per_step, "eval": launches_eval},
+        "clocks": clk,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        v, sample = wl.oracle_sample()
+        out["cpu_baseline"] = {"value": round(v, 4), "unit": wl.unit, "cores": 1, "kind": "oracle",
+                               "sample": sample}
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def run_reference(args, rank, world):
+    """The CPU oracle as the reference arm: rank 0 only, bounded samples."""
+    if rank != 0:
+        return
+    wl = make_workload(args.workload, "auto")
+    # inputs only (no GPU): build the host arrays the oracle needs
+    from paper_2507_13204_gb300 import workloads as W
+    from oracle import oracle as O
+    O.build()
+    if isinstance(wl, DenseWL):
+        A, x = W.quadform_inputs(wl.n, seed=0)
+        rows = 1000
+        A = A[:rows].copy()
+        unit_bytes = wl.es * (rows * wl.n + 2 * wl.n)
+        fn = lambda: O.quadform_grad(A, x)
+        sample = f"value+grad of the first {rows} rows of the {wl.n}x{wl.n} problem per step"
+        to_value = lambda s: unit_bytes / 1e9 / s
+    elif isinstance(wl, TetWL):
+        mesh, u = W.tet_inputs(wl.a)
+        ne = 500_000
+        conn, G = mesh.conn[:ne], mesh.G[:ne]
+        unit_bytes = ne * (16 + 12 * wl.es) + 2 * mesh.nv * wl.es
+        fn = lambda: O.tet_grad(conn, G, u)
+        sample = f"value+grad of the first {ne} tets of the {wl.a}^3 mesh per step"
+        to_value = lambda s: unit_bytes / 1e9 / s
+    else:
+        x, b = W.laplace1d_inputs(wl.n)
+        fn = lambda: O.laplace1d_grad(x, b)
+        sample = f"one value+grad at n={wl.n} per step"
+        to_value = lambda s: 1.0 / s
+    for _ in range(args.warmup):
+        fn()
+    K = args.steps if args.steps > 0 else 10
+    t0 = time.perf_counter()
+    for _ in range(K):
+        fn()
+    s = (time.perf_counter() - t0) / K
+    v = to_value(s)
+    out = {"metric": METRIC, "value": round(v, 5), "unit": wl.unit, "n_gpus": world, "steps": K,
+           "warmup": args.warmup, "ms_per_step": round(s * 1e3, 4), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype_name,
+           "data": "synthetic (seeded numpy PCG64 draws)", "config": wl.config(),
+           "impl": "reference",
+           "cpu_baseline": {"value": round(v, 5), "unit": wl.unit, "cores": 1, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": round(v, 5), "unit": wl.unit, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,240 @@
+/*
+ * kg.h -- C ABI of libkg.so: reverse-mode gradients of data-parallel functions
+ * on one GB300 GPU (sm_103a).
+ *
+ * The method is that of Liegeois et al., "Performance Portable Gradient
+ * Computations Using Source Transformation" (arXiv 2507.13204):
+ *   - a gradient call runs the forward pass of the function and then its
+ *     reverse pass (Sec. 3, opening paragraph of "Methodology");
+ *   - the reverse of a sum reduction is a broadcast of the output adjoint
+ *     (Sec. 3.2, reverse of deep_copy(view, scalar) and the parallel_sum
+ *     helper); the output adjoint ("seed") defaults to 1 as in the paper's
+ *     generated gradient (Sec. 4, Fig. "grad_f");
+ *   - a read through an index map becomes a scatter-add of adjoints, which the
+ *     paper makes atomic (Sec. 3.3, race-detection rules); this library offers
+ *     that atomic scatter and an atomic-free gather over the transposed
+ *     connectivity, the rescheduling the paper proposes as future work
+ *     (Sec. 5, first restriction);
+ *   - forward values needed by the reverse pass are recomputed or read from a
+ *     tape allocated once outside the kernels (Sec. 5, third restriction).
+ *
+ * Problems ("kinds"):
+ *   KG_QUADFORM   f(x; A) = ||A x||^2, A dense m x n, row-major.  Forward is a
+ *                 team-per-row parallel_reduce then a sum reduction.
+ *   KG_TETENERGY  f(u; conn, G) = sum_e log1p(|G_e u_e|^2): u_e gathers the 4
+ *                 vertex values of tet e through conn (an index map), G_e is
+ *                 the 3x4 matrix of P1 barycentric gradients.
+ *   KG_LAPLACE1D  the paper's example (Sec. 4, Fig. "function_f"):
+ *                 f(x, b) = ||A (3 x) - b||^2, A = tridiag(-1, 2, -1).
+ *
+ * Conventions for every entry point:
+ *   - All data pointers are DEVICE pointers unless the name ends in _host.
+ *   - Element type is the problem's dtype (double for KG_F64, float for
+ *     KG_F32); index arrays are int32.  Scalars such as f and the seed are
+ *     single elements of that dtype, in device memory.
+ *   - Inputs given to kg_create (A, conn, G, b) are BORROWED: the caller owns
+ *     them and keeps them alive and unchanged-in-shape until kg_destroy.
+ *     All workspaces (partial sums, tape, transposed connectivity, error word)
+ *     are allocated by kg_create / kg_batch_create; the per-call entry points
+ *     kg_eval, kg_grad, kg_eval_tape, kg_grad_from_tape and kg_grad_batched
+ *     allocate nothing.
+ *   - Calls are asynchronous on the given stream (NULL = legacy default
+ *     stream) and do not synchronise the host, except kg_create,
+ *     kg_batch_create, kg_sync and the *_host entry points, which do.
+ *   - Calls on one problem must be ordered on one stream: they share the
+ *     problem's workspace.
+ *   - Every entry point returns a kg_status and never aborts; on failure a
+ *     message is kept per host thread and returned by kg_last_error().
+ *     Device-side failures (out-of-range connectivity when checks are on, a
+ *     bounded wait that ran out) set a sticky error word that kg_sync reads.
+ */
+#ifndef KG_H
+#define KG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same object as cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st *kg_stream;
+
+typedef enum {
+  KG_OK = 0,
+  KG_ERR_INVALID_ARG = 1, /* bad size, NULL pointer, misaligned pointer, bad enum */
+  KG_ERR_OOM = 2,         /* a workspace allocation failed (nothing is leaked) */
+  KG_ERR_CUDA = 3,        /* a CUDA runtime call failed; message has the CUDA error */
+  KG_ERR_BOUNDS = 4,      /* connectivity entry outside [0, N_v) */
+  KG_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
+  KG_ERR_UNSUPPORTED = 6, /* option combination not implemented for this kind */
+  KG_ERR_STATE = 7        /* call out of order (e.g. kg_grad_from_tape before a tape exists) */
+} kg_status;
+
+typedef enum { KG_QUADFORM = 1, KG_TETENERGY = 2, KG_LAPLACE1D = 3 } kg_kind;
+typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
+
+/* Reverse-pass schedule for gathers (Sec. 3.3 and Sec. 5).
+ *   ATOMIC    reuse the forward schedule; scatter-adds are atomic adds.
+ *   CSR       (tet) atomic-free: per-element adjoints go to a tape, then each
+ *             vertex gathers its incident entries through the transposed
+ *             connectivity built at kg_create; bitwise run-to-run reproducible.
+ *   TRANSPOSE (dense) a second kernel reads A by columns: xbar = A^T ybar.
+ *   FUSED     (dense) one pass over A: each team computes y_i, broadcasts
+ *             ybar_i and accumulates ybar_i A_i,: into private partials that a
+ *             second tiny kernel sums in a fixed order; reproducible.
+ *   AUTO      FUSED for dense, ATOMIC for tets, the stencil transpose for 1-D. */
+typedef enum {
+  KG_STRATEGY_AUTO = 0,
+  KG_STRATEGY_ATOMIC = 1,
+  KG_STRATEGY_CSR = 2,
+  KG_STRATEGY_TRANSPOSE = 3,
+  KG_STRATEGY_FUSED = 4
+} kg_strategy;
+
+/* Forward values for the reverse pass (Sec. 5, taping restriction).
+ *   RECOMPUTE  kg_grad reruns the forward pass inside the gradient kernel.
+ *   TAPE       kg_create allocates a tape (tet: the per-element adjoint
+ *              c_e = G_e^T (2 g_e / (1 + |g_e|^2)), N_e x 4 values);
+ *              kg_eval_tape fills it and kg_grad_from_tape consumes it.
+ *   AUTO       TAPE when the tape fits tape_budget_bytes, else RECOMPUTE. */
+typedef enum { KG_MODE_AUTO = 0, KG_MODE_RECOMPUTE = 1, KG_MODE_TAPE = 2 } kg_mode;
+
+/* FP64 arithmetic.  GB300 has few FP64 units (about 2 FMA per clock per SM),
+ * so FP64 kernels can run their arithmetic as pairs of FP32 values
+ * (hi + lo, at least 47 significant bits) on the FP32 units.
+ *   NATIVE  FP64 instructions throughout.
+ *   PAIR    FP32-pair arithmetic for the streamed products and sums
+ *           (results within 1e-12 relative L2 of exact FP64 arithmetic for
+ *           inputs in the normal FP32 exponent range); kernels that have no
+ *           pair variant use NATIVE.
+ *   AUTO    PAIR where a pair variant exists. */
+typedef enum { KG_ARITH_AUTO = 0, KG_ARITH_NATIVE = 1, KG_ARITH_PAIR = 2 } kg_arith;
+
+typedef struct {
+  int dtype;                /* kg_dtype */
+  int strategy;             /* kg_strategy */
+  int mode;                 /* kg_mode */
+  int arith;                /* kg_arith (FP64 only) */
+  int check;                /* 1: kernels bounds-check conn and set KG_ERR_BOUNDS */
+  int block;                /* threads per CTA; 0 = tuned default */
+  int team;                 /* dense: threads per row team (32 or block); 0 = tuned */
+  int tile;                 /* elements (tet) or rows (dense) per work tile; 0 = tuned */
+  size_t tape_budget_bytes; /* cap for KG_MODE_AUTO; 0 = 1 GiB */
+} kg_options;
+
+typedef struct kg_problem kg_problem;
+typedef struct kg_batch kg_batch;
+
+/* Fills *opt with defaults: KG_F64, AUTO strategy/mode/arith, check = 0. */
+void kg_options_default(kg_options *opt);
+
+/* Create a problem (Sec. 3.1: shadow storage for every intermediate is
+ * allocated once, here, never inside the per-call entry points).
+ *   kind   kg_kind.
+ *   sizes  KG_QUADFORM: {n} (square) or {m, n};  KG_TETENERGY: {N_e, N_v};
+ *          KG_LAPLACE1D: {n}.  All sizes >= 1 and < 2^31.
+ *   data   device pointers, borrowed: KG_QUADFORM {A (m*n, row-major)};
+ *          KG_TETENERGY {conn (int32, N_e*4), G (N_e*12, row-major 3x4 per
+ *          element: G[e*12 + r*4 + k] = d lambda_k / d x_r)};
+ *          KG_LAPLACE1D {b (n)}.  Each must be 16-byte aligned.
+ *   opt    NULL for defaults.
+ * Validates conn against [0, N_v) (KG_ERR_BOUNDS), builds the transposed
+ * connectivity when the CSR strategy is selected, and synchronises `s`. */
+kg_status kg_create(kg_problem **out, int kind, const int64_t *sizes, int nsizes,
+                    const void *const *data, int ndata, const kg_options *opt, kg_stream s);
+
+/* Forward pass only: *f = f(x).  x: n (QUADFORM, LAPLACE1D) or N_v (TET). */
+kg_status kg_eval(kg_problem *p, const void *x, void *f, kg_stream s);
+
+/* Value and gradient (the paper's gradient function: forward pass, seed,
+ * reverse pass; Sec. 4, Fig. "grad_f").
+ *   x      input (device), length n or N_v.
+ *   f      nullable; receives f(x).
+ *   gx     gradient w.r.t. x, length n or N_v.
+ *   gdata  nullable; gradient w.r.t. the first data operand: A (m*n,
+ *          QUADFORM) or b (n, LAPLACE1D).  KG_ERR_UNSUPPORTED for TET.
+ *   seed   nullable device scalar: the output adjoint fbar (NULL means 1).
+ *   accumulate  0: gx/gdata are overwritten; 1: the gradient is added to
+ *          them (the "_d_x +=" convention of the generated code). */
+kg_status kg_grad(kg_problem *p, const void *x, void *f, void *gx, void *gdata,
+                  const void *seed, int accumulate, kg_stream s);
+
+/* TET, TAPE mode: forward pass that also records the per-element adjoint
+ * factors c_e (for fbar = 1) in the problem's tape.  f nullable. */
+kg_status kg_eval_tape(kg_problem *p, const void *x, void *f, kg_stream s);
+
+/* TET, TAPE mode: reverse pass from the tape written by the last
+ * kg_eval_tape: gx[v] (+)= fbar * sum over incidences (e,k) of v of c_e[k],
+ * by atomic scatter or by the CSR gather (the problem's strategy).  Reads no
+ * G.  KG_ERR_STATE if no tape was recorded. */
+kg_status kg_grad_from_tape(kg_problem *p, void *gx, const void *seed, int accumulate,
+                            kg_stream s);
+
+/* End-to-end variant of kg_grad on HOST buffers: copies x (pageable or
+ * pinned host memory) to the device, runs kg_grad with seed 1 on `s`, copies
+ * f and gx back and synchronises `s`.  f_host nullable. */
+kg_status kg_grad_host(kg_problem *p, const void *x_host, void *f_host, void *gx_host,
+                       kg_stream s);
+
+/* Batched value-and-gradient of many independent problems (QUADFORM and
+ * TETENERGY, FP64 or FP32, all of one dtype) in ONE persistent kernel launch
+ * driven by a device work queue of (instance, tile) items, captured once in a
+ * CUDA graph and replayed (Sec. 5, second restriction: fewer launches and
+ * host synchronisation points).  kg_batch_create autotunes the tile and team
+ * sizes (cached in $KG_TUNE_CACHE, default ~/.cache/kg_tune.json, keyed by GPU
+ * name, kind and size bucket), builds the work table and synchronises `s`.
+ * The problems are borrowed and must outlive the batch. */
+kg_status kg_batch_create(kg_batch **out, kg_problem *const *probs, int count,
+                          const kg_options *opt, kg_stream s);
+
+/* x[i], f[i], gx[i]: device pointers for instance i (f[i] nullable).  The
+ * pointer tables are host arrays of `count` entries; they are copied into the
+ * batch's device table (a graph replay if unchanged since the last call). */
+kg_status kg_grad_batched(kg_batch *b, const void *const *x, void *const *f, void *const *gx,
+                          kg_stream s);
+
+/* Same work as kg_grad_batched, issued as one kg_grad launch sequence per
+ * instance on `s` (the per-instance launch loop the batch is compared with). */
+kg_status kg_grad_batched_loop(kg_batch *b, const void *const *x, void *const *f,
+                               void *const *gx, kg_stream s);
+
+/* Synchronises the problem's last stream and reads its sticky device error
+ * word (cleared by the read): KG_ERR_BOUNDS, KG_ERR_TIMEOUT or KG_OK. */
+kg_status kg_sync(kg_problem *p);
+kg_status kg_batch_sync(kg_batch *b);
+
+/* Message for the last failure on this host thread ("" if none). */
+const char *kg_last_error(void);
+
+/* The configuration kg_create resolved from the options (AUTO replaced by the
+ * choice made): kg_strategy, kg_mode and kg_arith.  Any pointer may be NULL. */
+kg_status kg_get_config(const kg_problem *p, int *strategy, int *mode, int *arith);
+
+/* Bytes of device workspace owned by the problem (tape, CSR, partials). */
+size_t kg_workspace_bytes(const kg_problem *p);
+
+/* Number of kernel launches the last per-call entry point issued on this
+ * host thread (for launch accounting in benchmarks). */
+int kg_last_launch_count(void);
+
+/* Main-kernel timing for benchmarks.  While enabled (on this host thread),
+ * every per-call entry point brackets its main kernel (the fused forward /
+ * reverse kernel; not the small reduction or zero-fill launches) with CUDA
+ * events recorded on the launch stream.  kg_profile_read waits for the
+ * recorded events and returns the summed kernel time in milliseconds and the
+ * number of bracketed launches since the last kg_profile_enable(1); name
+ * receives a static string naming the last bracketed kernel.  Up to 65536
+ * launches are kept; later ones are not timed.  Not for use inside CUDA graph
+ * capture. */
+kg_status kg_profile_enable(int on);
+kg_status kg_profile_read(double *ms, int *launches, const char **name);
+
+void kg_destroy(kg_problem *p);
+void kg_batch_destroy(kg_batch *b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KG_H */

@@ -1,0 +1,176 @@
+"""Problem objects over the C ABI (argument marshalling only).
+
+A Problem keeps the tensors it lent to kg_create alive for as long as the
+handle exists, allocates output tensors with torch on the problem's device and
+calls the library.  No arithmetic of the method happens here.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import _lib as L
+
+_DT = {torch.float64: L.KG_F64, torch.float32: L.KG_F32}
+STRATEGIES = {"auto": L.KG_STRATEGY_AUTO, "atomic": L.KG_STRATEGY_ATOMIC, "csr": L.KG_STRATEGY_CSR,
+              "transpose": L.KG_STRATEGY_TRANSPOSE, "fused": L.KG_STRATEGY_FUSED}
+MODES = {"auto": L.KG_MODE_AUTO, "recompute": L.KG_MODE_RECOMPUTE, "tape": L.KG_MODE_TAPE}
+ARITHS = {"auto": L.KG_ARITH_AUTO, "native": L.KG_ARITH_NATIVE, "pair": L.KG_ARITH_PAIR}
+
+
+def _dev_tensor(t: torch.Tensor, dtype=None) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError("kg: problem data must be CUDA tensors")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"kg: expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("kg: tensors must be contiguous")
+    return t
+
+
+class Problem:
+    kind = 0
+
+    def __init__(self, sizes, data, dtype: torch.dtype, strategy="auto", mode="auto",
+                 arith="auto", check=False, block=0, team=0, tile=0, tape_budget_bytes=0,
+                 stream=None):
+        self.dtype = dtype
+        self.device = data[0].device
+        self._data = list(data)  # borrowed by the library: keep alive
+        opt = L.options(dtype=_DT[dtype], strategy=STRATEGIES[strategy], mode=MODES[mode],
+                        arith=ARITHS[arith], check=int(bool(check)), block=block, team=team,
+                        tile=tile, tape_budget_bytes=tape_budget_bytes)
+        with torch.cuda.device(self.device):
+            self.handle = L.kg_create(self.kind, sizes, self._data, opt, stream)
+        self.sizes = tuple(int(s) for s in sizes)
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "handle", None):
+            L.kg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- shapes
+    @property
+    def nx(self) -> int:
+        raise NotImplementedError
+
+    def _scalar(self):
+        return torch.empty((), dtype=self.dtype, device=self.device)
+
+    # -- calls
+    def eval(self, x, f=None, stream=None):
+        f = self._scalar() if f is None else f
+        L.kg_eval(self.handle, _dev_tensor(x, self.dtype), f, stream)
+        return f
+
+    def grad(self, x, gx=None, f=None, gdata=None, seed=None, accumulate=False, stream=None):
+        gx = torch.empty(self.nx, dtype=self.dtype, device=self.device) if gx is None else gx
+        f = self._scalar() if f is None else f
+        L.kg_grad(self.handle, _dev_tensor(x, self.dtype), f, gx, gdata, seed, int(accumulate), stream)
+        return f, gx
+
+    def grad_host(self, x_host, gx_host, f_host=None, stream=None):
+        L.kg_grad_host(self.handle, x_host, f_host, gx_host, stream)
+
+    def sync(self):
+        L.kg_sync(self.handle)
+
+    @property
+    def config(self):
+        """Resolved (strategy, mode, arith)."""
+        return L.kg_get_config(self.handle)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return L.kg_workspace_bytes(self.handle)
+
+
+class QuadForm(Problem):
+    """f(x) = ||A x||^2, A (m x n) row-major on the device."""
+    kind = L.KG_QUADFORM
+
+    def __init__(self, A: torch.Tensor, **kw):
+        A = _dev_tensor(A)
+        m, n = A.shape
+        super().__init__([m, n], [A], A.dtype, **kw)
+        self.m, self.n = m, n
+
+    @property
+    def nx(self):
+        return self.n
+
+
+class TetEnergy(Problem):
+    """f(u) = sum_e log1p(|G_e u_e|^2); conn int32 [N_e, 4], G [N_e, 12]."""
+    kind = L.KG_TETENERGY
+
+    def __init__(self, conn: torch.Tensor, G: torch.Tensor, nv: int, **kw):
+        conn = _dev_tensor(conn, torch.int32)
+        G = _dev_tensor(G)
+        if conn.shape[-1] != 4 or G.shape[-1] != 12 or conn.shape[0] != G.shape[0]:
+            raise ValueError("kg: conn must be [N_e, 4] and G [N_e, 12]")
+        super().__init__([conn.shape[0], nv], [conn, G], G.dtype, **kw)
+        self.ne, self.nv = int(conn.shape[0]), int(nv)
+
+    @property
+    def nx(self):
+        return self.nv
+
+    def eval_tape(self, u, f=None, stream=None):
+        f = self._scalar() if f is None else f
+        L.kg_eval_tape(self.handle, _dev_tensor(u, self.dtype), f, stream)
+        return f
+
+    def grad_from_tape(self, gx=None, seed=None, accumulate=False, stream=None):
+        gx = torch.empty(self.nv, dtype=self.dtype, device=self.device) if gx is None else gx
+        L.kg_grad_from_tape(self.handle, gx, seed, int(accumulate), stream)
+        return gx
+
+
+class Laplace1D(Problem):
+    """The paper's example f(x, b) = ||A (3x) - b||^2, A = tridiag(-1, 2, -1)."""
+    kind = L.KG_LAPLACE1D
+
+    def __init__(self, b: torch.Tensor, **kw):
+        b = _dev_tensor(b)
+        super().__init__([b.shape[0]], [b], b.dtype, **kw)
+        self.n = int(b.shape[0])
+
+    @property
+    def nx(self):
+        return self.n
+
+
+class Batch:
+    """Many problems differentiated by one persistent launch (graph-replayed)."""
+
+    def __init__(self, problems, block=0, tile=0, stream=None):
+        self.problems = list(problems)
+        opt = L.options(dtype=_DT[self.problems[0].dtype], block=block, tile=tile)
+        self.handle = L.kg_batch_create([p.handle for p in self.problems], opt, stream)
+
+    def grad(self, xs, fs, gxs, stream=None):
+        L.kg_grad_batched(self.handle, xs, fs, gxs, stream)
+
+    def grad_loop(self, xs, fs, gxs, stream=None):
+        L.kg_grad_batched_loop(self.handle, xs, fs, gxs, stream)
+
+    def sync(self):
+        L.kg_batch_sync(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            L.kg_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,104 @@
+// Internal declarations shared by the translation units of libkg.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/kg.h"
+
+namespace kg {
+
+// Bits of the sticky device error word.
+enum : unsigned { ERRBIT_BOUNDS = 1u, ERRBIT_TIMEOUT = 2u };
+
+// Status + thread-local message.
+kg_status fail(kg_status st, const std::string& msg);
+kg_status cuda_fail(cudaError_t e, const char* what);
+void count_launch(int k = 1);
+// Main-kernel timing (kg_profile_enable): brackets one launch with events.
+void prof_begin(cudaStream_t s, const char* name);
+void prof_end(cudaStream_t s);
+void reset_launch_count();
+
+// Allocation through one hook so that tests can force an allocation failure
+// (environment variable KG_TEST_FAIL_ALLOC=N fails the N-th allocation).
+cudaError_t dev_alloc(void** p, size_t bytes);
+
+int num_sms();
+
+// Launch configuration of one dense row-team kernel.
+struct QfConfig {
+  int block = 256;  // threads per CTA
+  int team = 256;   // threads per row team (32..block, power of 2)
+  int cpt = 1;      // columns per team thread (compile-time variant)
+  int grid = 1;     // CTAs
+  int rows_per_cta = 1;
+};
+
+struct kg_problem_impl;
+}  // namespace kg
+
+// Problem handle.  All device workspaces are owned here and allocated in
+// kg_create; per-call entry points only launch kernels.
+struct kg_problem {
+  int kind = 0;
+  int dtype = KG_F64;
+  kg_options opt{};
+  int strategy = KG_STRATEGY_AUTO;  // resolved strategy
+  int mode = KG_MODE_RECOMPUTE;     // resolved mode
+  int arith = KG_ARITH_NATIVE;      // resolved FP64 arithmetic
+  int64_t m = 0, n = 0;             // QUADFORM m x n; TET m = N_e, n = N_v; LAPLACE1D n
+  const void* data0 = nullptr;      // A | conn | b
+  const void* data1 = nullptr;      // - | G | -
+  size_t esize = 8;
+
+  // workspaces
+  std::vector<void*> allocs;
+  size_t ws_bytes = 0;
+  void* partials = nullptr;  // dense: [grid][n] of T (FUSED / TRANSPOSE)
+  double* fpart = nullptr;   // per-CTA f partials
+  int fpart_len = 0;
+  unsigned* counter = nullptr;
+  unsigned* err = nullptr;   // sticky error word
+  void* y = nullptr;         // dense / 1-D: forward intermediates
+  void* tape = nullptr;      // tet: c_e [N_e][4]
+  bool tape_valid = false;
+  int* rowptr = nullptr;     // tet CSR: [N_v + 1]
+  int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k
+  void* xdev = nullptr;      // kg_grad_host staging
+  void* gdev = nullptr;
+  void* fdev = nullptr;
+
+  kg::QfConfig qf;           // dense launch configuration
+  int tet_block = 256, tet_grid = 1;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace kg {
+// Per-kind entry points (defined in quadform.cu, tet.cu, laplace1d.cu).
+kg_status qf_setup(kg_problem* p, cudaStream_t s);
+kg_status qf_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
+kg_status qf_grad(kg_problem* p, const void* x, void* f, void* gx, void* gA, const void* seed,
+                  int accumulate, cudaStream_t s);
+
+kg_status tet_setup(kg_problem* p, cudaStream_t s);
+kg_status tet_eval(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s);
+kg_status tet_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
+                   int accumulate, cudaStream_t s);
+kg_status tet_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,
+                             cudaStream_t s);
+
+kg_status lap_setup(kg_problem* p, cudaStream_t s);
+kg_status lap_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
+kg_status lap_grad(kg_problem* p, const void* x, void* f, void* gx, void* gb, const void* seed,
+                   int accumulate, cudaStream_t s);
+
+// Workspace helper: allocate, record for kg_destroy, count bytes.
+kg_status ws_alloc(kg_problem* p, void** out, size_t bytes, const char* what);
+// Error word, arrival counter and `fpart_len` per-CTA f partials, zeroed on `s`.
+kg_status ws_common(kg_problem* p, int fpart_len, cudaStream_t s);
+}  // namespace kg

@@ -1,0 +1,104 @@
+"""GPU parity: dense ||A x||^2 value and gradient through the C ABI vs the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2507_13204_gb300 import workloads as W
+from tests.helpers import TOL, f32_round, rel_l2, rel_scalar
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api(cuda_ok):
+    from paper_2507_13204_gb300 import build
+    build.build()
+    from paper_2507_13204_gb300 import api as A
+    return A
+
+
+def _run(api, A, x, dtype, strategy, want_gA=False, seed=None, accumulate=False, **kw):
+    dev = torch.device("cuda")
+    At = torch.tensor(A, dtype=dtype, device=dev)
+    xt = torch.tensor(x, dtype=dtype, device=dev)
+    p = api.QuadForm(At, strategy=strategy, **kw)
+    gx = torch.full((A.shape[1],), 0.5, dtype=dtype, device=dev)
+    gA = torch.full(A.shape, 0.25, dtype=dtype, device=dev) if want_gA else None
+    sd = None if seed is None else torch.tensor(seed, dtype=dtype, device=dev)
+    f, gx = p.grad(xt, gx=gx, gdata=gA, seed=sd, accumulate=accumulate)
+    fe = p.eval(xt)
+    torch.cuda.synchronize()
+    p.sync()
+    out = (f.item(), gx.cpu().numpy(), fe.item(), None if gA is None else gA.cpu().numpy())
+    p.close()
+    return out
+
+
+SHAPES = [(64, 64), (1, 1), (1, 37), (257, 1), (1000, 777), (300, 2048), (129, 5000), (40, 12288)]
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+@pytest.mark.parametrize("strategy", ["fused", "atomic", "transpose"])
+def test_f64_matches_oracle(api, m, n, strategy):
+    A, x = W.quadform_inputs(n, m=m, seed=m * 7 + n)
+    f_ref, g_ref = O.quadform_grad(A, x)
+    f, gx, fe, _ = _run(api, A, x, torch.float64, strategy)
+    assert rel_scalar(f, f_ref) <= TOL["f64"]
+    assert rel_scalar(fe, f_ref) <= TOL["f64"]
+    assert rel_l2(gx, g_ref) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("m,n", [(64, 64), (1000, 777), (129, 5000), (10000, 10000)])
+@pytest.mark.parametrize("strategy", ["fused", "transpose"])
+def test_f32_matches_oracle_on_rounded_inputs(api, m, n, strategy):
+    A, x = W.quadform_inputs(n, m=m, seed=3)
+    A32, x32 = f32_round(A), f32_round(x)
+    f_ref, g_ref = O.quadform_grad(A32, x32)
+    f, gx, fe, _ = _run(api, A32, x32, torch.float32, strategy)
+    assert rel_scalar(f, f_ref) <= TOL["f32"]
+    assert rel_scalar(fe, f_ref) <= TOL["f32"]
+    assert rel_l2(gx, g_ref) <= TOL["f32"]
+
+
+def test_cfg1_gradient_wrt_A_seed_and_accumulate(api):
+    # the 64 x 64 workload: gradient w.r.t. x and A, output adjoint 1.7, accumulate onto
+    # the 0.5 / 0.25 prefill (the "_d_x +=" convention)
+    A, x = W.quadform_inputs(64, seed=0)
+    f_ref, g_ref, gA_ref = O.quadform_grad(A, x, fbar=1.7, want_gA=True)
+    f, gx, _, gA = _run(api, A, x, torch.float64, "fused", want_gA=True, seed=1.7, accumulate=True)
+    assert rel_scalar(f, f_ref) <= TOL["f64"]
+    assert rel_l2(gx - 0.5, g_ref) <= TOL["f64"]
+    assert rel_l2(gA - 0.25, gA_ref) <= TOL["f64"]
+
+
+def test_full_size_n10000_f64(api):
+    # the 10000 x 10000 FP64 workload (800 MB), every gradient entry checked
+    A, x = W.quadform_inputs(10000, seed=0)
+    f_ref, g_ref = O.quadform_grad(A, x)
+    for strategy in ("fused", "transpose"):
+        f, gx, fe, _ = _run(api, A, x, torch.float64, strategy)
+        assert rel_scalar(f, f_ref) <= TOL["f64"], strategy
+        assert rel_scalar(fe, f_ref) <= TOL["f64"], strategy
+        assert rel_l2(gx, g_ref) <= TOL["f64"], strategy
+
+
+def test_fused_is_bitwise_reproducible(api):
+    A, x = W.quadform_inputs(3000, m=2000, seed=9)
+    a = _run(api, A, x, torch.float64, "fused")
+    b = _run(api, A, x, torch.float64, "fused")
+    assert a[0] == b[0] and np.array_equal(a[1], b[1])
+
+
+def test_identity_special_case_exact(api):
+    x = np.random.default_rng(1).uniform(-1, 1, 500)
+    f, gx, _, _ = _run(api, np.eye(500), x, torch.float64, "fused")
+    assert np.array_equal(gx, 2 * x)
+
+
+def test_n_beyond_row_team_is_unsupported_for_fused(api):
+    from paper_2507_13204_gb300 import _lib as L
+    A = torch.zeros((2, 20000), dtype=torch.float64, device="cuda")
+    with pytest.raises(L.KGError) as ei:
+        api.QuadForm(A, strategy="fused")
+    assert ei.value.status == L.KG_ERR_UNSUPPORTED

@@ -1,0 +1,148 @@
+"""GPU parity: tet-mesh energy value and gradient (atomic scatter and CSR gather,
+recompute and tape) through the C ABI vs the CPU oracle."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2507_13204_gb300 import workloads as W
+from tests.helpers import TOL, f32_round, rel_l2, rel_scalar
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api(cuda_ok):
+    from paper_2507_13204_gb300 import build
+    build.build()
+    from paper_2507_13204_gb300 import api as A
+    return A
+
+
+def _problem(api, mesh, dtype, **kw):
+    conn = torch.tensor(mesh.conn, device="cuda")
+    G = torch.tensor(mesh.G, dtype=dtype, device="cuda")
+    return api.TetEnergy(conn, G, mesh.nv, **kw)
+
+
+MESHES = [(1, None), (3, 2), (7, None), (12, 2), (25, 2)]
+
+
+@pytest.mark.parametrize("a,jit", MESHES)
+@pytest.mark.parametrize("strategy", ["atomic", "csr"])
+def test_f64_grad_matches_oracle(api, a, jit, strategy):
+    mesh = W.tet_mesh(a, jitter_seed=jit, perm_seed=a)
+    u = np.random.default_rng(a).uniform(-1, 1, mesh.nv)
+    f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u, fbar=1.0)
+    p = _problem(api, mesh, torch.float64, strategy=strategy)
+    ut = torch.tensor(u, device="cuda")
+    f, g = p.grad(ut)
+    fe = p.eval(ut)
+    p.sync()
+    assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+    assert rel_scalar(fe.item(), f_ref) <= TOL["f64"]
+    assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("strategy", ["atomic", "csr"])
+def test_f32_matches_oracle_on_rounded_inputs(api, strategy):
+    mesh = W.tet_mesh(20, jitter_seed=2, perm_seed=3)
+    u = np.random.default_rng(5).uniform(-1, 1, mesh.nv)
+    G32, u32 = f32_round(mesh.G), f32_round(u)
+    f_ref, g_ref = O.tet_grad(mesh.conn, G32, u32)
+    conn = torch.tensor(mesh.conn, device="cuda")
+    p = api.TetEnergy(conn, torch.tensor(G32, dtype=torch.float32, device="cuda"), mesh.nv,
+                      strategy=strategy)
+    f, g = p.grad(torch.tensor(u32, dtype=torch.float32, device="cuda"))
+    p.sync()
+    assert rel_scalar(f.item(), f_ref) <= TOL["f32"]
+    assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("strategy", ["atomic", "csr"])
+def test_tape_mode_seed_and_accumulate(api, strategy):
+    mesh = W.tet_mesh(9, jitter_seed=2, perm_seed=4)
+    u = np.random.default_rng(6).uniform(-1, 1, mesh.nv)
+    f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u, fbar=-0.6)
+    p = _problem(api, mesh, torch.float64, strategy=strategy, mode="tape")
+    ut = torch.tensor(u, device="cuda")
+    f = p.eval_tape(ut)
+    seed = torch.tensor(-0.6, dtype=torch.float64, device="cuda")
+    g = torch.full((mesh.nv,), 2.0, dtype=torch.float64, device="cuda")
+    p.grad_from_tape(gx=g, seed=seed, accumulate=True)
+    p.sync()
+    assert rel_scalar(f.item(), O.tet_value(mesh.conn, mesh.G, u)) <= TOL["f64"]
+    assert rel_l2(g.cpu().numpy() - 2.0, g_ref) <= TOL["f64"]
+
+
+def test_tape_before_record_is_a_state_error(api):
+    from paper_2507_13204_gb300 import _lib as L
+    mesh = W.tet_mesh(2)
+    p = _problem(api, mesh, torch.float64, mode="tape")
+    with pytest.raises(L.KGError) as ei:
+        p.grad_from_tape()
+    assert ei.value.status == L.KG_ERR_STATE
+
+
+def test_csr_is_bitwise_reproducible_and_close_to_atomic(api):
+    mesh = W.tet_mesh(15, jitter_seed=2, perm_seed=8)
+    u = torch.tensor(np.random.default_rng(7).uniform(-1, 1, mesh.nv), device="cuda")
+    pc = _problem(api, mesh, torch.float64, strategy="csr")
+    pa = _problem(api, mesh, torch.float64, strategy="atomic")
+    g1 = pc.grad(u)[1].clone()
+    g2 = pc.grad(u)[1].clone()
+    ga = pa.grad(u)[1]
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+    assert rel_l2(ga.cpu().numpy(), g1.cpu().numpy()) <= TOL["f64"]
+
+
+def test_linear_field_interior_gradient_vanishes(api):
+    mesh = W.tet_mesh(6, perm_seed=2)
+    a = np.array([0.2, -0.4, 0.1])
+    p = _problem(api, mesh, torch.float64)
+    f, g = p.grad(torch.tensor(W.linear_field(mesh, a), device="cuda"))
+    gi = np.rint(mesh.coords).astype(int)
+    interior = np.all((gi > 0) & (gi < 6), axis=1)
+    assert rel_scalar(f.item(), mesh.ne * np.log1p(a @ a)) <= TOL["f64"]
+    assert np.max(np.abs(g.cpu().numpy()[interior])) < 1e-13
+
+
+def test_full_size_100_cubed_f64(api):
+    # the 6e6-tet, 1.03e6-vertex relabelled mesh; every gradient entry checked
+    mesh, u = W.tet_inputs(100)
+    f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
+    ut = torch.tensor(u, device="cuda")
+    for strategy in ("atomic", "csr"):
+        p = _problem(api, mesh, torch.float64, strategy=strategy)
+        f, g = p.grad(ut)
+        fe = p.eval(ut)
+        p.sync()
+        assert rel_scalar(f.item(), f_ref) <= TOL["f64"], strategy
+        assert rel_scalar(fe.item(), f_ref) <= TOL["f64"], strategy
+        assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"], strategy
+        p.close()
+
+
+def test_bad_connectivity_rejected_at_create(api):
+    from paper_2507_13204_gb300 import _lib as L
+    mesh = W.tet_mesh(2)
+    conn = mesh.conn.copy()
+    conn[5, 2] = mesh.nv + 3
+    with pytest.raises(L.KGError) as ei:
+        api.TetEnergy(torch.tensor(conn, device="cuda"),
+                      torch.tensor(mesh.G, device="cuda"), mesh.nv)
+    assert ei.value.status == L.KG_ERR_BOUNDS
+
+
+def test_checked_kernels_flag_connectivity_changed_after_create(api):
+    from paper_2507_13204_gb300 import _lib as L
+    mesh = W.tet_mesh(3)
+    conn = torch.tensor(mesh.conn, device="cuda")
+    p = api.TetEnergy(conn, torch.tensor(mesh.G, device="cuda"), mesh.nv, check=True)
+    conn[4, 1] = mesh.nv + 10  # the checked kernel skips the element and records the error
+    p.grad(torch.zeros(mesh.nv, dtype=torch.float64, device="cuda"))
+    with pytest.raises(L.KGError) as ei:
+        p.sync()
+    assert ei.value.status == L.KG_ERR_BOUNDS
+    p.sync()  # the sticky word was cleared by the read
