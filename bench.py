@@ -334,23 +334,23 @@ class LaplaceWL(Workload):
         return reps / (time.perf_counter() - t0), f"{reps} x value+grad at n={self.n} (oracle, 1 thread)"
 
 
-def make_workload(name: str, arith: str):
+def make_workload(name: str, arith: str, size: int = 0):
     if name == "dense":
-        return DenseWL(10000, "f64", arith=arith)
+        return DenseWL(size or 10000, "f64", arith=arith)
     if name == "dense32":
-        return DenseWL(10000, "f32")
+        return DenseWL(size or 10000, "f32")
     if name == "dense64":
         return DenseWL(64, "f64", arith=arith)
     if name == "tet":
-        return TetWL(100, "f64", arith=arith)
+        return TetWL(size or 100, "f64", arith=arith)
     if name == "tet32":
-        return TetWL(100, "f32")
+        return TetWL(size or 100, "f32")
     if name == "tetcsr":
-        return TetWL(100, "f64", strategy="csr", arith=arith)
+        return TetWL(size or 100, "f64", strategy="csr", arith=arith)
     if name == "laplace":
-        return LaplaceWL(10000)
+        return LaplaceWL(size or 10000)
     if name == "laplace_atomic":
-        return LaplaceWL(10000, strategy="atomic")
+        return LaplaceWL(size or 10000, strategy="atomic")
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -363,6 +363,9 @@ def main():
     ap.add_argument("--impl", default="kg", choices=["kg", "reference"])
     ap.add_argument("--workload", default="dense")
     ap.add_argument("--arith", default="auto", choices=["auto", "native", "pair"])
+    ap.add_argument("--size", type=int, default=0,
+                    help="problem size override (dense n, tet cubes per axis, 1-D n) for small "
+                         "profiling cases; the default is the full workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -388,7 +391,7 @@ def main():
         B.build()
     if dist:
         dist.barrier()
-    wl = make_workload(args.workload, args.arith)
+    wl = make_workload(args.workload, args.arith, args.size)
     wl.setup(dev)
     stream = torch.cuda.current_stream()
     peaks = load_peaks()
@@ -519,7 +522,7 @@ def run_reference(args, rank, world):
     """The CPU oracle as the reference arm: rank 0 only, bounded samples."""
     if rank != 0:
         return
-    wl = make_workload(args.workload, "auto")
+    wl = make_workload(args.workload, "auto", args.size)
     # inputs only (no GPU): build the host arrays the oracle needs
     from paper_2507_13204_gb300 import workloads as W
     from oracle import oracle as O
