@@ -69,7 +69,9 @@ typedef enum {
   KG_ERR_BOUNDS = 4,      /* connectivity entry outside [0, N_v) */
   KG_ERR_TIMEOUT = 5,     /* a bounded device wait gave up */
   KG_ERR_UNSUPPORTED = 6, /* option combination not implemented for this kind */
-  KG_ERR_STATE = 7        /* call out of order (e.g. kg_grad_from_tape before a tape exists) */
+  KG_ERR_STATE = 7,       /* call out of order (e.g. kg_grad_from_tape before a tape exists) */
+  KG_ERR_RANGE = 8        /* PAIR arithmetic: an input outside 0 or [2^-60, 2^40) in magnitude;
+                             the results of that call are invalid (rerun with KG_ARITH_NATIVE) */
 } kg_status;
 
 typedef enum { KG_QUADFORM = 1, KG_TETENERGY = 2, KG_LAPLACE1D = 3 } kg_kind;
@@ -201,7 +203,8 @@ kg_status kg_grad_batched_loop(kg_batch *b, const void *const *x, void *const *f
                                void *const *gx, kg_stream s);
 
 /* Synchronises the problem's last stream and reads its sticky device error
- * word (cleared by the read): KG_ERR_BOUNDS, KG_ERR_TIMEOUT or KG_OK. */
+ * word (cleared by the read): KG_ERR_BOUNDS, KG_ERR_TIMEOUT, KG_ERR_RANGE or
+ * KG_OK. */
 kg_status kg_sync(kg_problem *p);
 kg_status kg_batch_sync(kg_batch *b);
 

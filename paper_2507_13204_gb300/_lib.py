@@ -15,9 +15,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libkg.so")
 
 KG_OK, KG_ERR_INVALID_ARG, KG_ERR_OOM, KG_ERR_CUDA, KG_ERR_BOUNDS, KG_ERR_TIMEOUT, \
-    KG_ERR_UNSUPPORTED, KG_ERR_STATE = range(8)
+    KG_ERR_UNSUPPORTED, KG_ERR_STATE, KG_ERR_RANGE = range(9)
 STATUS_NAMES = ["KG_OK", "KG_ERR_INVALID_ARG", "KG_ERR_OOM", "KG_ERR_CUDA", "KG_ERR_BOUNDS",
-                "KG_ERR_TIMEOUT", "KG_ERR_UNSUPPORTED", "KG_ERR_STATE"]
+                "KG_ERR_TIMEOUT", "KG_ERR_UNSUPPORTED", "KG_ERR_STATE", "KG_ERR_RANGE"]
 KG_QUADFORM, KG_TETENERGY, KG_LAPLACE1D = 1, 2, 3
 KG_F64, KG_F32 = 0, 1
 KG_STRATEGY_AUTO, KG_STRATEGY_ATOMIC, KG_STRATEGY_CSR, KG_STRATEGY_TRANSPOSE, KG_STRATEGY_FUSED = range(5)

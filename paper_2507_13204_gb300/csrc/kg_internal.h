@@ -13,7 +13,7 @@
 namespace kg {
 
 // Bits of the sticky device error word.
-enum : unsigned { ERRBIT_BOUNDS = 1u, ERRBIT_TIMEOUT = 2u };
+enum : unsigned { ERRBIT_BOUNDS = 1u, ERRBIT_TIMEOUT = 2u, ERRBIT_RANGE = 4u };
 
 // Status + thread-local message.
 kg_status fail(kg_status st, const std::string& msg);
@@ -84,6 +84,14 @@ kg_status qf_setup(kg_problem* p, cudaStream_t s);
 kg_status qf_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status qf_grad(kg_problem* p, const void* x, void* f, void* gx, void* gA, const void* seed,
                   int accumulate, cudaStream_t s);
+
+// float-pair dense kernels (quadform_pair.cu)
+bool qf_pair_supported(const kg_problem* p);
+kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok);
+int qf_pair_grid(const kg_problem* p, int* band);
+kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
+kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
+                       int accumulate, cudaStream_t s);
 
 kg_status tet_setup(kg_problem* p, cudaStream_t s);
 kg_status tet_eval(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s);

@@ -323,19 +323,47 @@ static int transpose_chunks(const kg_problem* p) {
 
 kg_status qf_setup(kg_problem* p, cudaStream_t s) {
   int var = pick_variant(p->n, p->opt.team);
-  if (p->strategy == KG_STRATEGY_AUTO) p->strategy = var >= 0 ? KG_STRATEGY_FUSED : KG_STRATEGY_TRANSPOSE;
   if (p->strategy == KG_STRATEGY_CSR)
     return fail(KG_ERR_UNSUPPORTED, "QUADFORM: the CSR strategy is for index-map gathers (TETENERGY)");
+  if (p->mode == KG_MODE_TAPE)
+    return fail(KG_ERR_UNSUPPORTED, "QUADFORM: the reverse pass needs only y; no tape mode");
+  p->mode = KG_MODE_RECOMPUTE;
+
+  // FP64 arithmetic: float pairs on the FP32 units when the kernel and the data allow
+  bool pair = false;
+  if (p->dtype == KG_F64 && p->arith != KG_ARITH_NATIVE) {
+    const bool shape_ok = qf_pair_supported(p) && p->n >= 1024 && p->opt.team == 0;
+    if (!shape_ok && p->arith == KG_ARITH_PAIR)
+      return fail(KG_ERR_UNSUPPORTED, "QUADFORM PAIR arithmetic needs the FUSED strategy, even n "
+                                      "and 1024 <= n <= 12288");
+    if (shape_ok) {
+      kg_status rc = ws_common(p, num_sms(), s);
+      if (rc != KG_OK) return rc;
+      bool in_range = false;
+      if ((rc = qf_pair_range_ok(p, s, &in_range)) != KG_OK) return rc;
+      if (!in_range && p->arith == KG_ARITH_PAIR)
+        return fail(KG_ERR_UNSUPPORTED, "QUADFORM PAIR arithmetic: A has entries outside "
+                                        "0 or [2^-60, 2^40) in magnitude");
+      pair = in_range;
+    }
+  }
+  if (pair) {
+    p->arith = KG_ARITH_PAIR;
+    p->strategy = KG_STRATEGY_FUSED;
+    QfConfig& c = p->qf;
+    c.grid = qf_pair_grid(p, &c.rows_per_cta);
+    c.team = c.block = 512;
+    kg_status rc = ws_alloc(p, &p->partials, 8 * (size_t)c.grid * p->n, "xbar partials (pairs)");
+    return rc;
+  }
+  if (p->arith == KG_ARITH_AUTO || p->dtype == KG_F32) p->arith = KG_ARITH_NATIVE;
+  if (p->strategy == KG_STRATEGY_AUTO) p->strategy = var >= 0 ? KG_STRATEGY_FUSED : KG_STRATEGY_TRANSPOSE;
   if (var < 0) {
     if (p->strategy != KG_STRATEGY_TRANSPOSE)
       return fail(KG_ERR_UNSUPPORTED, "QUADFORM: n = " + std::to_string(p->n) +
                                           " exceeds the row-team variants (n <= 12288); use TRANSPOSE");
     return fail(KG_ERR_UNSUPPORTED, "QUADFORM: n > 12288 is not supported by the forward kernel");
   }
-  if (p->mode == KG_MODE_TAPE)
-    return fail(KG_ERR_UNSUPPORTED, "QUADFORM: the reverse pass needs only y; no tape mode");
-  p->mode = KG_MODE_RECOMPUTE;
-  if (p->arith == KG_ARITH_AUTO) p->arith = KG_ARITH_NATIVE;
   const QfVariant& v = kVariants[var];
   QfConfig& c = p->qf;
   c.team = v.team;
@@ -391,6 +419,7 @@ static kg_status qf_eval_t(kg_problem* p, const void* x, void* f, T* y, cudaStre
 }
 
 kg_status qf_eval(kg_problem* p, const void* x, void* f, cudaStream_t s) {
+  if (p->arith == KG_ARITH_PAIR) return qf_pair_eval(p, x, f, s);
   return p->dtype == KG_F64 ? qf_eval_t<double>(p, x, f, nullptr, s)
                             : qf_eval_t<float>(p, x, f, nullptr, s);
 }
@@ -451,6 +480,12 @@ static kg_status qf_grad_t(kg_problem* p, const void* x, void* f, void* gx, void
 
 kg_status qf_grad(kg_problem* p, const void* x, void* f, void* gx, void* gA, const void* seed,
                   int accumulate, cudaStream_t s) {
+  if (p->arith == KG_ARITH_PAIR) {
+    if (gA)
+      return fail(KG_ERR_UNSUPPORTED, "QUADFORM: the gradient w.r.t. A is produced by the native "
+                                      "kernels (create the problem with KG_ARITH_NATIVE)");
+    return qf_pair_grad(p, x, f, gx, seed, accumulate, s);
+  }
   return p->dtype == KG_F64 ? qf_grad_t<double>(p, x, f, gx, gA, seed, accumulate, s)
                             : qf_grad_t<float>(p, x, f, gx, gA, seed, accumulate, s);
 }

@@ -1,0 +1,398 @@
+// Dense ||A x||^2 value-and-gradient for FP64 data with float-pair arithmetic.
+//
+// Same method as quadform.cu (forward row dot products y_i, broadcast of the
+// reduction adjoint ybar_i = 2 fbar y_i, reverse xbar_j += A_ij ybar_i with
+// one pass over A), laid out for GB300:
+//   - one CTA of 16 warps per SM;
+//   - whole rows of A stream into a two-stage shared-memory ring through TMA
+//     bulk copies (cp.async.bulk + mbarrier transaction counts), the rows two
+//     ahead are prefetched into L2; warps release a stage through an "empty"
+//     mbarrier and thread 0, once every warp has released it, issues the copy
+//     of the row two ahead into it;
+//   - consumer thread t owns the column pairs jp = t + 512 k; it splits A's
+//     doubles into float pairs (integer instructions), writes the split values
+//     back in place so the reverse pass does not split again, and accumulates
+//     with FMA two-product / TwoSum on the FP32 units;
+//   - the private xbar partials (float pairs) of each CTA go to a workspace that
+//     a second kernel sums in a fixed order: bitwise reproducible.
+// All waits are bounded (about one second) and report KG_ERR_TIMEOUT.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <string>
+
+#include "kg_device.cuh"
+#include "kg_internal.h"
+#include "kg_pair.cuh"
+
+namespace kg {
+
+constexpr int QP_CW = 16;                    // warps
+constexpr int QP_CT = QP_CW * 32;            // threads
+constexpr int QP_THREADS = QP_CT;
+constexpr int QP_BAR = 1;                    // named barrier id
+
+struct QpArgs {
+  const double* A;
+  const double* x;
+  int64_t m;
+  int n;  // even
+  int band;
+  const double* seed;
+  float4* partials;  // [grid][n/2] of (h0, l0, h1, l1)
+  double* fpart;
+  unsigned* counter;
+  double* f;  // EVAL: written by the last CTA
+  unsigned* err;
+};
+
+__device__ __forceinline__ Acc shfl_xor_acc(Acc a, int o) {
+  Acc b;
+  b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
+  b.l = __shfl_xor_sync(0xffffffffu, a.l, o);
+  return b;
+}
+
+template <int PPT, bool FUSED>
+__global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int n = a.n, npairs = n >> 1;
+  double* stage0 = reinterpret_cast<double*>(smem);
+  double* stage1 = stage0 + n;
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage1 + n);
+  uint64_t* empty = full + 2;
+  Acc* red = reinterpret_cast<Acc*>(empty + 2);  // [2][QP_CW]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(red + 2 * QP_CW);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * a.band;
+  const int64_t r1 = r0 + a.band < a.m ? r0 + a.band : a.m;
+  const int nrows = r1 > r0 ? (int)(r1 - r0) : 0;
+  const uint32_t row_bytes = (uint32_t)n * 8u;
+
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    mbar_init(&empty[0], QP_CW);
+    mbar_init(&empty[1], QP_CW);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+  // thread 0 issues the copies: rows 0 and 1 now, row it+2 once stage it&1 is released
+  int issued = 0;
+  if (threadIdx.x == 0) {
+    for (int it = 0; it < 2 && it < nrows; ++it) {
+      const double* src = a.A + (r0 + it) * (int64_t)n;
+      mbar_arrive_expect_tx(&full[it], row_bytes);
+      tma_load_1d(it ? stage1 : stage0, src, row_bytes, &full[it]);
+      ++issued;
+      if (it + 2 < nrows) prefetch_l2_bulk(src + 2 * (int64_t)n, row_bytes);
+    }
+  }
+
+  // ------------------------------------------------------------ consumers
+  const int t = threadIdx.x;
+  float xh[PPT][2], xl[PPT][2];
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) {
+    const int jp = t + QP_CT * k;
+    double2 xv = make_double2(0.0, 0.0);
+    if (jp < npairs) xv = reinterpret_cast<const double2*>(a.x)[jp];
+    bad |= !pair_in_range(xv.x) || !pair_in_range(xv.y);
+    const Pair p0 = split_f64(xv.x), p1 = split_f64(xv.y);
+    xh[k][0] = p0.h;
+    xl[k][0] = p0.l;
+    xh[k][1] = p1.h;
+    xl[k][1] = p1.l;
+  }
+  const double fb = a.seed ? *a.seed : 1.0;
+  if (FUSED) bad |= !pair_in_range(2.0 * fb);
+  if (bad) set_error(a.err, ERRBIT_RANGE);
+  const Pair fb2 = split_f64(2.0 * fb);
+
+  Acc xb[PPT][2];
+#pragma unroll
+  for (int k = 0; k < PPT; ++k) xb[k][0] = xb[k][1] = acc_zero();
+  double fsum = 0.0;
+
+  for (int it = 0; it < nrows; ++it) {
+    const int s = it & 1;
+    const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1);
+    double2* rowd = reinterpret_cast<double2*>(s ? stage1 : stage0);
+    float4* rowf = reinterpret_cast<float4*>(rowd);
+    Acc y0 = acc_zero(), y1 = acc_zero();
+    if (ok) {
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const int jp = t + QP_CT * k;
+        if (jp < npairs) {
+          const double2 v = rowd[jp];
+          const Pair p0 = split_f64(v.x), p1 = split_f64(v.y);
+          if (FUSED) rowf[jp] = make_float4(p0.h, p0.l, p1.h, p1.l);
+          acc_fma(y0, p0.h, p0.l, xh[k][0], xl[k][0]);
+          acc_fma(y1, p1.h, p1.l, xh[k][1], xl[k][1]);
+        }
+      }
+    }
+    Acc yv = acc_add(y0, y1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) yv = acc_add(yv, shfl_xor_acc(yv, o));
+    if (lane == 0) red[(it & 1) * QP_CW + warp] = yv;
+    // all consumers: partials written; the OR tells everyone whether a wait gave up
+    if (named_barrier_or(QP_BAR, QP_CT, !ok)) {
+      if (lane == 0 && warp == 0) set_error(a.err, ERRBIT_TIMEOUT);
+      *abort_flag = 1;
+      break;
+    }
+    Acc ya = lane < QP_CW ? red[(it & 1) * QP_CW + lane] : acc_zero();
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) ya = acc_add(ya, shfl_xor_acc(ya, o));
+    const Pair y = acc_pair(ya);
+    if (t == 0) {
+      const double yd = pair_to_double(y);
+      fsum += yd * yd;
+    }
+    if (FUSED) {
+      const Pair yb = pair_mul(fb2, y);
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const int jp = t + QP_CT * k;
+        if (jp < npairs) {
+          const float4 q = rowf[jp];
+          acc_fma(xb[k][0], q.x, q.y, yb.h, yb.l);
+          acc_fma(xb[k][1], q.z, q.w, yb.h, yb.l);
+        }
+      }
+      if ((it & 15) == 15) {
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          acc_renorm(xb[k][0]);
+          acc_renorm(xb[k][1]);
+        }
+      }
+      fence_proxy_async_smem();  // split values were written with generic stores
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (threadIdx.x == 0 && it + 2 < nrows && !*abort_flag) {
+      if (!mbar_wait_bounded(&empty[s], (it >> 1) & 1)) {
+        set_error(a.err, ERRBIT_TIMEOUT);
+        *abort_flag = 1;
+      } else {
+        const double* src = a.A + (r0 + it + 2) * (int64_t)n;
+        mbar_arrive_expect_tx(&full[s], row_bytes);
+        tma_load_1d(s ? stage1 : stage0, src, row_bytes, &full[s]);
+        ++issued;
+        if (it + 4 < nrows) prefetch_l2_bulk(src + 2 * (int64_t)n, row_bytes);
+      }
+    }
+    __syncwarp();
+  }
+  // do not leave with a copy into this CTA's shared memory in flight
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < 2; ++st) {
+      const int last = issued - 1 - ((issued - 1 - st) & 1);  // last row copied into stage st
+      if (last >= 0) mbar_wait_bounded(&full[st], (last >> 1) & 1);
+    }
+  }
+
+  if (FUSED) {
+    float4* out = a.partials + (int64_t)blockIdx.x * npairs;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      const int jp = t + QP_CT * k;
+      if (jp < npairs) {
+        const Pair p0 = acc_pair(xb[k][0]), p1 = acc_pair(xb[k][1]);
+        out[jp] = make_float4(p0.h, p0.l, p1.h, p1.l);
+      }
+    }
+    if (t == 0) a.fpart[blockIdx.x] = fsum;
+  } else if (t == 0) {
+    // last CTA to arrive sums the f partials in CTA order
+    a.fpart[blockIdx.x] = fsum;
+    __threadfence();
+    const unsigned arrived = atomicAdd(a.counter, 1u);
+    if (arrived == gridDim.x - 1) {
+      __threadfence();
+      double tot = 0.0;
+      for (int i = 0; i < (int)gridDim.x; ++i) tot += __ldcg(&a.fpart[i]);
+      *a.f = tot;
+      *a.counter = 0u;
+    }
+  }
+}
+
+// Fixed-order sum of the per-CTA float-pair partials: thread (cx, py) adds
+// partials py, py+16, ... of column pair cx; the 16 sums are then added in py
+// order and converted to double once per column.  Block 0 also writes f.
+__global__ void __launch_bounds__(512) qf_pair_reduce_kernel(const float4* __restrict__ partials,
+                                                             int nparts, int npairs,
+                                                             const double* __restrict__ fpart,
+                                                             double* gx, double* f, int accumulate) {
+  constexpr int CX = 32, PY = 16;
+  __shared__ Acc red[PY][CX][2];
+  __shared__ double fred[32];
+  const int cx = threadIdx.x % CX, py = threadIdx.x / CX;
+  const int jp = blockIdx.x * CX + cx;
+  Acc s0 = acc_zero(), s1 = acc_zero();
+  if (jp < npairs) {
+    for (int c = py; c < nparts; c += PY) {
+      const float4 v = partials[(int64_t)c * npairs + jp];
+      s0 = acc_add(s0, Acc{v.x, v.y});
+      s1 = acc_add(s1, Acc{v.z, v.w});
+    }
+  }
+  red[py][cx][0] = s0;
+  red[py][cx][1] = s1;
+  __syncthreads();
+  if (py == 0 && jp < npairs) {
+    Acc t0 = red[0][cx][0], t1 = red[0][cx][1];
+#pragma unroll
+    for (int i = 1; i < PY; ++i) {
+      t0 = acc_add(t0, red[i][cx][0]);
+      t1 = acc_add(t1, red[i][cx][1]);
+    }
+    const double g0 = pair_to_double(acc_pair(t0)), g1 = pair_to_double(acc_pair(t1));
+    double2* o = reinterpret_cast<double2*>(gx) + jp;
+    if (accumulate) {
+      const double2 old = *o;
+      *o = make_double2(old.x + g0, old.y + g1);
+    } else {
+      *o = make_double2(g0, g1);
+    }
+  }
+  if (blockIdx.x == 0 && f) {
+    double fs = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) fs += fpart[i];
+    fs = block_sum(fs, fred);
+    if (threadIdx.x == 0) *f = fs;
+  }
+}
+
+// Sets ERRBIT_RANGE when some entry is outside the pair arithmetic's range.
+__global__ void pair_range_scan_kernel(const double2* __restrict__ p, int64_t n2, unsigned* err) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const double2 v = __ldcs(p + i);
+    bad |= !pair_in_range(v.x) || !pair_in_range(v.y);
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_error(err, ERRBIT_RANGE);
+}
+
+// ---------------------------------------------------------------- host ----
+static int pair_ppt(int64_t n) {
+  const int64_t need = (n / 2 + QP_CT - 1) / QP_CT;
+  for (int p : {1, 2, 4, 6, 8, 10, 12})
+    if (need <= p) return p;
+  return -1;
+}
+
+bool qf_pair_supported(const kg_problem* p) {
+  return p->dtype == KG_F64 && (p->n % 2) == 0 && pair_ppt(p->n) > 0 &&
+         (p->strategy == KG_STRATEGY_FUSED || p->strategy == KG_STRATEGY_AUTO);
+}
+
+static size_t pair_smem(int n) {
+  return (size_t)2 * n * 8 + 4 * 8 + 2 * QP_CW * sizeof(Acc) + 16;
+}
+
+// Scans A once (create time) for values outside the pair range; returns true if
+// every value is representable.
+kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok) {
+  const int64_t n2 = p->m * p->n / 2;
+  cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), s);
+  if (e != cudaSuccess) return cuda_fail(e, "pair range scan");
+  int grid = (int)std::min<int64_t>((n2 + 255) / 256, (int64_t)num_sms() * 8);
+  pair_range_scan_kernel<<<std::max(grid, 1), 256, 0, s>>>(
+      static_cast<const double2*>(p->data0), n2, p->err);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pair range scan");
+  unsigned h = 0;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "pair range scan");
+  if ((e = cudaMemcpy(&h, p->err, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "pair range scan");
+  if ((e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), s)) != cudaSuccess)
+    return cuda_fail(e, "pair range scan");
+  *ok = (h & ERRBIT_RANGE) == 0;
+  return KG_OK;
+}
+
+int qf_pair_grid(const kg_problem* p, int* band) {
+  const int64_t g = std::min<int64_t>(p->m, num_sms());
+  const int64_t b = (p->m + g - 1) / g;
+  *band = (int)b;
+  return (int)((p->m + b - 1) / b);
+}
+
+template <int PPT, bool FUSED>
+static cudaError_t launch_pair(int grid, size_t smem, cudaStream_t s, const QpArgs& a) {
+  auto kern = qf_pair_kernel<PPT, FUSED>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, QP_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool FUSED>
+static cudaError_t dispatch_pair(int ppt, int grid, size_t smem, cudaStream_t s, const QpArgs& a) {
+  switch (ppt) {
+    case 1: return launch_pair<1, FUSED>(grid, smem, s, a);
+    case 2: return launch_pair<2, FUSED>(grid, smem, s, a);
+    case 4: return launch_pair<4, FUSED>(grid, smem, s, a);
+    case 6: return launch_pair<6, FUSED>(grid, smem, s, a);
+    case 8: return launch_pair<8, FUSED>(grid, smem, s, a);
+    case 10: return launch_pair<10, FUSED>(grid, smem, s, a);
+    case 12: return launch_pair<12, FUSED>(grid, smem, s, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
+static QpArgs pair_args(kg_problem* p, const void* x, const void* seed) {
+  QpArgs a{};
+  a.A = static_cast<const double*>(p->data0);
+  a.x = static_cast<const double*>(x);
+  a.m = p->m;
+  a.n = (int)p->n;
+  a.band = p->qf.rows_per_cta;
+  a.seed = static_cast<const double*>(seed);
+  a.partials = static_cast<float4*>(p->partials);
+  a.fpart = p->fpart;
+  a.counter = p->counter;
+  a.err = p->err;
+  return a;
+}
+
+kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0)
+    return fail(KG_ERR_INVALID_ARG, "QUADFORM pair kernels need a 16-byte aligned x");
+  QpArgs a = pair_args(p, x, nullptr);
+  a.f = static_cast<double*>(f);
+  prof_begin(s, "qf_pair_kernel<eval>");
+  cudaError_t e = dispatch_pair<false>(pair_ppt(p->n), p->qf.grid, pair_smem((int)p->n), s, a);
+  prof_end(s);
+  count_launch();
+  return e == cudaSuccess ? KG_OK : cuda_fail(e, "qf pair forward kernel");
+}
+
+kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
+                       int accumulate, cudaStream_t s) {
+  if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0 || (reinterpret_cast<uintptr_t>(gx) & 15u) != 0)
+    return fail(KG_ERR_INVALID_ARG, "QUADFORM pair kernels need 16-byte aligned x and gx");
+  QpArgs a = pair_args(p, x, seed);
+  prof_begin(s, "qf_pair_kernel<fused>");
+  cudaError_t e = dispatch_pair<true>(pair_ppt(p->n), p->qf.grid, pair_smem((int)p->n), s, a);
+  prof_end(s);
+  count_launch();
+  if (e != cudaSuccess) return cuda_fail(e, "qf pair fused kernel");
+  const int npairs = (int)(p->n / 2);
+  qf_pair_reduce_kernel<<<(npairs + 31) / 32, 512, 0, s>>>(
+      static_cast<const float4*>(p->partials), p->qf.grid, npairs, p->fpart,
+      static_cast<double*>(gx), static_cast<double*>(f), accumulate);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "qf pair reduce kernel");
+  return KG_OK;
+}
+
+}  // namespace kg

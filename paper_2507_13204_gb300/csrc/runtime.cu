@@ -377,6 +377,8 @@ kg_status kg_sync(kg_problem* p) {
   }
   if (h & ERRBIT_BOUNDS) return fail(KG_ERR_BOUNDS, "device: connectivity entry outside [0, N_v)");
   if (h & ERRBIT_TIMEOUT) return fail(KG_ERR_TIMEOUT, "device: a bounded wait gave up");
+  if (h & ERRBIT_RANGE)
+    return fail(KG_ERR_RANGE, "device: an input is outside the float-pair range (0 or 2^-60 <= |v| < 2^40)");
   return KG_OK;
 }
 

@@ -102,3 +102,76 @@ def test_n_beyond_row_team_is_unsupported_for_fused(api):
     with pytest.raises(L.KGError) as ei:
         api.QuadForm(A, strategy="fused")
     assert ei.value.status == L.KG_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("m,n", [(10000, 10000), (333, 1024), (5, 12288), (1000, 4098)])
+def test_pair_and_native_arithmetic_both_match(api, m, n):
+    A, x = W.quadform_inputs(n, m=m, seed=n + m)
+    f_ref, g_ref = O.quadform_grad(A, x, fbar=0.75)
+    dev = torch.device("cuda")
+    At = torch.tensor(A, device=dev)
+    xt = torch.tensor(x, device=dev)
+    seed = torch.tensor(0.75, dtype=torch.float64, device=dev)
+    for arith in ("pair", "native"):
+        p = api.QuadForm(At, arith=arith)
+        assert p.config[2] == arith
+        f, g = p.grad(xt, seed=seed)
+        fe = p.eval(xt)
+        p.sync()
+        assert rel_scalar(f.item(), f_ref) <= TOL["f64"], arith
+        assert rel_scalar(fe.item(), O.quadform_value(A, x)) <= TOL["f64"], arith
+        assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"], arith
+        p.close()
+
+
+def test_pair_is_default_for_f64_and_reproducible(api):
+    A, x = W.quadform_inputs(2048, m=700, seed=4)
+    p = api.QuadForm(torch.tensor(A, device="cuda"))
+    assert p.config == ("fused", "recompute", "pair")
+    xt = torch.tensor(x, device="cuda")
+    g1 = p.grad(xt)[1].clone()
+    g2 = p.grad(xt)[1].clone()
+    torch.cuda.synchronize()
+    assert torch.equal(g1, g2)
+
+
+def test_pair_range_rules(api):
+    from paper_2507_13204_gb300 import _lib as L
+    A, x = W.quadform_inputs(1024, m=64, seed=2)
+    A[3, 5] = 1e-70  # below the pair range: AUTO falls back to native FP64
+    At = torch.tensor(A, device="cuda")
+    p = api.QuadForm(At)
+    assert p.config[2] == "native"
+    f, g = p.grad(torch.tensor(x, device="cuda"))
+    p.sync()
+    assert rel_l2(g.cpu().numpy(), O.quadform_grad(A, x)[1]) <= TOL["f64"]
+    with pytest.raises(L.KGError) as ei:
+        api.QuadForm(At, arith="pair")
+    assert ei.value.status == L.KG_ERR_UNSUPPORTED
+    # an x out of range is reported by the pair kernel through kg_sync
+    A[3, 5] = 0.0
+    q = api.QuadForm(torch.tensor(A, device="cuda"), arith="pair")
+    xb = x.copy()
+    xb[7] = 1e300
+    q.grad(torch.tensor(xb, device="cuda"))
+    with pytest.raises(L.KGError) as ei:
+        q.sync()
+    assert ei.value.status == L.KG_ERR_RANGE
+    q.grad(torch.tensor(x, device="cuda"))
+    q.sync()
+
+
+def test_pair_exact_cases(api):
+    # zeros, identity and signed powers of two are exact in the pair representation
+    n = 2048
+    x = np.random.default_rng(3).uniform(-1, 1, n)
+    p = api.QuadForm(torch.tensor(np.eye(n), device="cuda"), arith="pair")
+    f, g = p.grad(torch.tensor(x, device="cuda"))
+    assert rel_l2(g.cpu().numpy(), 2 * x) <= 1e-15
+    A = np.zeros((8, n))
+    A[2, 100] = -4.0
+    A[5, 2047] = 0.5
+    q = api.QuadForm(torch.tensor(A, device="cuda"), arith="pair")
+    f, g = q.grad(torch.tensor(x, device="cuda"))
+    _, g_ref = O.quadform_grad(A, x)
+    assert rel_l2(g.cpu().numpy(), g_ref) <= 1e-15
