@@ -123,8 +123,8 @@ class Workload:
 
 
 class DenseWL(Workload):
-    def __init__(self, n, dtype, arith="auto", strategy="fused"):
-        self.n, self.m = n, n
+    def __init__(self, n, dtype, arith="auto", strategy="fused", m=None):
+        self.n, self.m = n, (m or n)
         self.dtype = dtype
         self.arith = arith
         self.strategy = strategy
@@ -134,7 +134,7 @@ class DenseWL(Workload):
     def setup(self, dev):
         import torch
         from paper_2507_13204_gb300 import api, workloads as W
-        A, x = W.quadform_inputs(self.n, seed=0)
+        A, x = W.quadform_inputs(self.n, m=self.m, seed=0)
         td = torch.float64 if self.dtype == "f64" else torch.float32
         self.At = torch.tensor(A, dtype=td, device=dev)
         self.xt = torch.tensor(x, dtype=td, device=dev)
@@ -334,11 +334,11 @@ class LaplaceWL(Workload):
         return reps / (time.perf_counter() - t0), f"{reps} x value+grad at n={self.n} (oracle, 1 thread)"
 
 
-def make_workload(name: str, arith: str, size: int = 0):
+def make_workload(name: str, arith: str, size: int = 0, rows: int = 0):
     if name == "dense":
-        return DenseWL(size or 10000, "f64", arith=arith)
+        return DenseWL(size or 10000, "f64", arith=arith, m=rows or None)
     if name == "dense32":
-        return DenseWL(size or 10000, "f32")
+        return DenseWL(size or 10000, "f32", m=rows or None)
     if name == "dense64":
         return DenseWL(64, "f64", arith=arith)
     if name == "tet":
@@ -366,6 +366,7 @@ def main():
     ap.add_argument("--size", type=int, default=0,
                     help="problem size override (dense n, tet cubes per axis, 1-D n) for small "
                          "profiling cases; the default is the full workload")
+    ap.add_argument("--rows", type=int, default=0, help="dense: rows of A (default: square)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -391,7 +392,7 @@ def main():
         B.build()
     if dist:
         dist.barrier()
-    wl = make_workload(args.workload, args.arith, args.size)
+    wl = make_workload(args.workload, args.arith, args.size, args.rows)
     wl.setup(dev)
     stream = torch.cuda.current_stream()
     peaks = load_peaks()
@@ -522,7 +523,7 @@ def run_reference(args, rank, world):
     """The CPU oracle as the reference arm: rank 0 only, bounded samples."""
     if rank != 0:
         return
-    wl = make_workload(args.workload, "auto", args.size)
+    wl = make_workload(args.workload, "auto", args.size, args.rows)
     # inputs only (no GPU): build the host arrays the oracle needs
     from paper_2507_13204_gb300 import workloads as W
     from oracle import oracle as O

@@ -148,7 +148,10 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
     }
     Acc ya = lane < QP_CW ? red[(it & 1) * QP_CW + lane] : acc_zero();
 #pragma unroll
-    for (int o = 8; o > 0; o >>= 1) ya = acc_add(ya, shfl_xor_acc(ya, o));
+    for (int o = QP_CW / 2; o > 0; o >>= 1) ya = acc_add(ya, shfl_xor_acc(ya, o));
+    // lanes 0..15 now hold the row total; give it to the whole warp
+    ya.s = __shfl_sync(0xffffffffu, ya.s, 0);
+    ya.l = __shfl_sync(0xffffffffu, ya.l, 0);
     const Pair y = acc_pair(ya);
     if (t == 0) {
       const double yd = pair_to_double(y);
