@@ -115,14 +115,14 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
   Acc xb[PPT][2];
 #pragma unroll
   for (int k = 0; k < PPT; ++k) xb[k][0] = xb[k][1] = acc_zero();
-  double fsum = 0.0;
+  Acc facc = acc_zero();
 
   for (int it = 0; it < nrows; ++it) {
     const int s = it & 1;
     const bool ok = mbar_wait_bounded(&full[s], (it >> 1) & 1);
     double2* rowd = reinterpret_cast<double2*>(s ? stage1 : stage0);
     float4* rowf = reinterpret_cast<float4*>(rowd);
-    Acc y0 = acc_zero(), y1 = acc_zero();
+    Acc yc[4] = {acc_zero(), acc_zero(), acc_zero(), acc_zero()};  // independent chains
     if (ok) {
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
@@ -131,12 +131,12 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
           const double2 v = rowd[jp];
           const Pair p0 = split_f64(v.x), p1 = split_f64(v.y);
           if (FUSED) rowf[jp] = make_float4(p0.h, p0.l, p1.h, p1.l);
-          acc_fma(y0, p0.h, p0.l, xh[k][0], xl[k][0]);
-          acc_fma(y1, p1.h, p1.l, xh[k][1], xl[k][1]);
+          acc_fma(yc[2 * (k & 1)], p0.h, p0.l, xh[k][0], xl[k][0]);
+          acc_fma(yc[2 * (k & 1) + 1], p1.h, p1.l, xh[k][1], xl[k][1]);
         }
       }
     }
-    Acc yv = acc_add(y0, y1);
+    Acc yv = acc_add(acc_add(yc[0], yc[1]), acc_add(yc[2], yc[3]));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) yv = acc_add(yv, shfl_xor_acc(yv, o));
     if (lane == 0) red[(it & 1) * QP_CW + warp] = yv;
@@ -153,9 +153,9 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
     ya.s = __shfl_sync(0xffffffffu, ya.s, 0);
     ya.l = __shfl_sync(0xffffffffu, ya.l, 0);
     const Pair y = acc_pair(ya);
-    if (t == 0) {
-      const double yd = pair_to_double(y);
-      fsum += yd * yd;
+    {  // f in pair arithmetic: no FP64 instruction in the row loop
+      const Pair y2 = pair_mul(y, y);
+      facc = acc_add(facc, Acc{y2.h, y2.l});
     }
     if (FUSED) {
       const Pair yb = pair_mul(fb2, y);
@@ -211,10 +211,10 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
         out[jp] = make_float4(p0.h, p0.l, p1.h, p1.l);
       }
     }
-    if (t == 0) a.fpart[blockIdx.x] = fsum;
+    if (t == 0) a.fpart[blockIdx.x] = acc_to_double(facc);
   } else if (t == 0) {
     // last CTA to arrive sums the f partials in CTA order
-    a.fpart[blockIdx.x] = fsum;
+    a.fpart[blockIdx.x] = acc_to_double(facc);
     __threadfence();
     const unsigned arrived = atomicAdd(a.counter, 1u);
     if (arrived == gridDim.x - 1) {
