@@ -87,11 +87,18 @@ kg_status qf_grad(kg_problem* p, const void* x, void* f, void* gx, void* gA, con
 
 // float-pair dense kernels (quadform_pair.cu)
 bool qf_pair_supported(const kg_problem* p);
+kg_status pair_range_ok(kg_problem* p, const double* data, int64_t count, cudaStream_t s, bool* ok);
 kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok);
 int qf_pair_grid(const kg_problem* p, int* band);
 kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
                        int accumulate, cudaStream_t s);
+
+// staged tet kernels (tet_pair.cu); mode 0 eval, 1 grad (atomic scatter), 2 tape
+int tet_staged_grid(const kg_problem* p);
+kg_status tet_staged_setup(kg_problem* p);
+kg_status tet_staged(kg_problem* p, int mode, const void* x, void* f, void* gx, const void* seed,
+                     cudaStream_t s);
 
 kg_status tet_setup(kg_problem* p, cudaStream_t s);
 kg_status tet_eval(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s);

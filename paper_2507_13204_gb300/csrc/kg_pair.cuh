@@ -175,3 +175,101 @@ __host__ __device__ __forceinline__ double acc_to_double(Acc a) {
 }
 
 }  // namespace kg
+
+// ---------------------------------------------------------------------------
+// Pair functions for the tet energy: sums, reciprocal, log1p, conversion.
+// ---------------------------------------------------------------------------
+namespace kg {
+
+// a + b for normalised pairs, normalised result.
+__host__ __device__ __forceinline__ Pair pair_add(Pair a, Pair b) {
+  float s, e;
+  two_sum(a.h, b.h, s, e);
+  e += a.l + b.l;
+  Pair r;
+  fast_two_sum(s, e, r.h, r.l);
+  return r;
+}
+
+// 1/t for t >= 1 (normalised pair): the correctly rounded float reciprocal r0
+// has relative error <= 2^-24; one Newton step r0 (1 + (1 - t r0)) in pair
+// form leaves an error of order 2^-48.
+__device__ __forceinline__ Pair pair_recip(Pair t) {
+  const float r0 = __frcp_rn(t.h);
+  float e = fmaf(-t.h, r0, 1.0f);
+  e = fmaf(-t.l, r0, e);
+  Pair r;
+  fast_two_sum(r0, r0 * e, r.h, r.l);
+  return r;
+}
+
+// Constants for pair_log1p, computed on the host from their definitions.
+struct LogConsts {
+  float ln2_h, ln2_l;      // ln 2 = ln2_h + ln2_l (a float pair)
+  float third_h, third_l;  // 1/3 as a pair
+};
+
+// Table entry k (0..255) for c_k = 1 + k/256: (log c_k as a pair, 1/c_k as a pair).
+constexpr int kLogTableSize = 256;
+
+// log1p(s) for s >= 0 given as a normalised pair; also returns t = 1 + s.
+// t = 2^E m with m in [1, 2); m = c_k (1 + r) with c_k = 1 + k/256 from the
+// top 8 mantissa bits, so |r| < 2^-8; log t = E ln2 + log c_k + log1p(r) with
+//   log1p(r) = r + r^2 (-1/2 + r/3) + r^4 (-1/4 + r/5 - r^2/6) + O(r^7),
+// the first three terms in pair precision and the rest in float.  Relative
+// error about 2^-46 (for s near 0, r = s exactly, so the result stays
+// relatively accurate).
+__host__ __device__ __forceinline__ Pair pair_log1p(Pair s, const float4* __restrict__ tab,
+                                           const LogConsts& K, Pair& t) {
+  float th, tl;
+  two_sum(1.0f, s.h, th, tl);
+  tl += s.l;
+  fast_two_sum(th, tl, th, tl);
+  t.h = th;
+  t.l = tl;
+  const uint32_t tb = f2u(th);
+  const int E = (int)((tb >> 23) & 0xFFu) - 127;            // t >= 1, so E >= 0
+  const float mh = u2f((tb & 0x007FFFFFu) | 0x3F800000u);  // th / 2^E
+  const float ml = tl * u2f((uint32_t)(127 - E) << 23);     // tl / 2^E (exact)
+  const uint32_t k = (f2u(mh) >> 15) & 0xFFu;
+  const float ck = u2f(0x3F800000u | (k << 15));
+  const float4 T = tab[k];
+  // d = m - c_k.  For t < 2 (E = 0) take it from s itself, d = (1 - c_k) + s,
+  // because the pair t = 1 + s drops the low bits of a small s; for t >= 2
+  // (s >= 1) d = (mh - c_k) + ml, where mh - c_k is exact (c_k <= mh < 2 c_k).
+  Pair d;
+  if (E == 0) {
+    d = pair_add(Pair{1.0f - ck, 0.0f}, s);
+  } else {
+    two_sum(mh - ck, ml, d.h, d.l);
+  }
+  const Pair r = pair_mul(d, Pair{T.z, T.w});
+  const Pair r2 = pair_mul(r, r);
+  const Pair u = pair_add(Pair{-0.5f, 0.0f}, pair_mul(r, Pair{K.third_h, K.third_l}));
+  const Pair v = pair_mul(r2, u);
+  const float q = fmaf(r.h, fmaf(-r.h, 0.16666667f, 0.2f), -0.25f);
+  const float w4 = (r2.h * r2.h) * q;
+  Pair lp = pair_add(r, v);
+  lp = pair_add(lp, Pair{w4, 0.0f});
+  const float Ef = (float)E;
+  const float p1 = Ef * K.ln2_h;                // E ln2_h as an exact pair (p1, e1)
+  const float e1 = fmaf(Ef, K.ln2_h, -p1);
+  Pair el;
+  fast_two_sum(p1, fmaf(Ef, K.ln2_l, e1), el.h, el.l);
+  return pair_add(pair_add(el, Pair{T.x, T.y}), lp);
+}
+
+// Exact float -> double with integer instructions (normal floats and zero).
+__device__ __forceinline__ double f32_to_f64_int(float f) {
+  const uint32_t b = f2u(f);
+  const uint32_t mag = b & 0x7FFFFFFFu;
+  const uint32_t hi = (b & 0x80000000u) | (mag ? (mag >> 3) + (896u << 20) : 0u);
+  return __hiloint2double((int)hi, (int)(b << 29));
+}
+
+// h + l as a double: two exact conversions on the integer units, one FP64 add.
+__device__ __forceinline__ double pair_to_double_fast(Pair p) {
+  return f32_to_f64_int(p.h) + f32_to_f64_int(p.l);
+}
+
+}  // namespace kg

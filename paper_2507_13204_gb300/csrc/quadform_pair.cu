@@ -302,15 +302,15 @@ static size_t pair_smem(int n) {
   return (size_t)2 * n * 8 + 4 * 8 + 2 * QP_CW * sizeof(Acc) + 16;
 }
 
-// Scans A once (create time) for values outside the pair range; returns true if
-// every value is representable.
-kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok) {
-  const int64_t n2 = p->m * p->n / 2;
+// Scans `count` doubles once (create time) for values outside the pair range;
+// *ok is true if every value is representable.  Count must be even.
+kg_status pair_range_ok(kg_problem* p, const double* data, int64_t count, cudaStream_t s, bool* ok) {
+  const int64_t n2 = count / 2;
   cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_fail(e, "pair range scan");
   int grid = (int)std::min<int64_t>((n2 + 255) / 256, (int64_t)num_sms() * 8);
-  pair_range_scan_kernel<<<std::max(grid, 1), 256, 0, s>>>(
-      static_cast<const double2*>(p->data0), n2, p->err);
+  pair_range_scan_kernel<<<std::max(grid, 1), 256, 0, s>>>(reinterpret_cast<const double2*>(data),
+                                                         n2, p->err);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pair range scan");
   unsigned h = 0;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "pair range scan");
@@ -320,6 +320,10 @@ kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok) {
     return cuda_fail(e, "pair range scan");
   *ok = (h & ERRBIT_RANGE) == 0;
   return KG_OK;
+}
+
+kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok) {
+  return pair_range_ok(p, static_cast<const double*>(p->data0), p->m * p->n, s, ok);
 }
 
 int qf_pair_grid(const kg_problem* p, int* band) {

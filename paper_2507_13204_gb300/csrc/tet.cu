@@ -21,108 +21,6 @@
 
 namespace kg {
 
-template <typename T>
-__device__ __forceinline__ T log1p_t(T v) {
-  if constexpr (sizeof(T) == 8) return log1p(v);
-  else return log1pf(v);
-}
-
-template <typename T>
-struct TetArgs {
-  const int4* conn;
-  const T* G;
-  const T* u;
-  int64_t ne;
-  int nv;
-  const T* seed;
-  T* gu;
-  T* tape;  // [ne][4]
-  double* fpart;
-  unsigned* counter;
-  T* f;
-  unsigned* err;
-  int check;
-};
-
-enum { TET_EVAL = 0, TET_GRAD = 1, TET_TAPE = 2 };
-
-// Loads the 12 entries of G_e (row-major 3x4) with 16-byte loads.
-template <typename T>
-__device__ __forceinline__ void load_G(const T* __restrict__ Ge, T g[12]) {
-  if constexpr (sizeof(T) == 8) {
-    const double2* p = reinterpret_cast<const double2*>(Ge);
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-      double2 v = __ldcs(p + i);
-      g[2 * i] = v.x;
-      g[2 * i + 1] = v.y;
-    }
-  } else {
-    const float4* p = reinterpret_cast<const float4*>(Ge);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      float4 v = __ldcs(p + i);
-      g[4 * i] = v.x;
-      g[4 * i + 1] = v.y;
-      g[4 * i + 2] = v.z;
-      g[4 * i + 3] = v.w;
-    }
-  }
-}
-
-// One thread per element (grid-stride).  EVAL: f.  GRAD: f and the atomic
-// scatter of fbar * c_e.  TAPE: f and c_e (fbar = 1) stored to the tape.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(256) tet_kernel(TetArgs<T> a) {
-  __shared__ double scratch[32];
-  const T fb = MODE == TET_GRAD ? load_seed(a.seed) : T(1);
-  T facc = T(0);
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < a.ne; e += stride) {
-    const int4 c = __ldcs(a.conn + e);
-    if (a.check) {
-      if ((unsigned)c.x >= (unsigned)a.nv || (unsigned)c.y >= (unsigned)a.nv ||
-          (unsigned)c.z >= (unsigned)a.nv || (unsigned)c.w >= (unsigned)a.nv) {
-        set_error(a.err, ERRBIT_BOUNDS);
-        continue;
-      }
-    }
-    T G[12];
-    load_G<T>(a.G + e * 12, G);
-    const T u0 = __ldg(a.u + c.x), u1 = __ldg(a.u + c.y), u2 = __ldg(a.u + c.z),
-            u3 = __ldg(a.u + c.w);
-    const T g0 = G[0] * u0 + G[1] * u1 + G[2] * u2 + G[3] * u3;
-    const T g1 = G[4] * u0 + G[5] * u1 + G[6] * u2 + G[7] * u3;
-    const T g2 = G[8] * u0 + G[9] * u1 + G[10] * u2 + G[11] * u3;
-    const T s = g0 * g0 + g1 * g1 + g2 * g2;
-    facc += log1p_t(s);
-    if constexpr (MODE != TET_EVAL) {
-      const T w = T(2) * fb / (T(1) + s);
-      const T w0 = w * g0, w1 = w * g1, w2 = w * g2;
-      const T c0 = G[0] * w0 + G[4] * w1 + G[8] * w2;
-      const T c1 = G[1] * w0 + G[5] * w1 + G[9] * w2;
-      const T c2 = G[2] * w0 + G[6] * w1 + G[10] * w2;
-      const T c3 = G[3] * w0 + G[7] * w1 + G[11] * w2;
-      if constexpr (MODE == TET_GRAD) {
-        atomicAdd(a.gu + c.x, c0);
-        atomicAdd(a.gu + c.y, c1);
-        atomicAdd(a.gu + c.z, c2);
-        atomicAdd(a.gu + c.w, c3);
-      } else {
-        T* t = a.tape + e * 4;
-        if constexpr (sizeof(T) == 8) {
-          __stcs(reinterpret_cast<double2*>(t), make_double2(c0, c1));
-          __stcs(reinterpret_cast<double2*>(t) + 1, make_double2(c2, c3));
-        } else {
-          __stcs(reinterpret_cast<float4*>(t), make_float4(c0, c1, c2, c3));
-        }
-      }
-    }
-  }
-  const double fcta = block_sum((double)facc, scratch);
-  finish_sum<T>(fcta, a.fpart, a.counter, a.f, 0, scratch);
-}
-
 // Reverse from the tape with the forward schedule: atomic scatter of fbar*c_e.
 template <typename T>
 __global__ void __launch_bounds__(256) tet_tape_scatter_kernel(const int4* __restrict__ conn,
@@ -252,15 +150,27 @@ kg_status tet_setup(kg_problem* p, cudaStream_t s) {
   const size_t tape_bytes = p->esize * 4 * (size_t)p->m;
   const size_t budget = p->opt.tape_budget_bytes ? p->opt.tape_budget_bytes : (size_t(1) << 30);
   if (p->mode == KG_MODE_AUTO) p->mode = tape_bytes <= budget ? KG_MODE_TAPE : KG_MODE_RECOMPUTE;
-  if (p->arith == KG_ARITH_AUTO) p->arith = KG_ARITH_NATIVE;
   p->tet_block = p->opt.block ? p->opt.block : 256;
   if (p->tet_block != 256) return fail(KG_ERR_UNSUPPORTED, "TETENERGY: block must be 256");
-  p->tet_grid = grid_for(p->m, p->tet_block, 8);
+  p->tet_grid = tet_staged_grid(p);
   kg_status rc = ws_common(p, p->tet_grid, s);
   if (rc != KG_OK) return rc;
   if (p->mode == KG_MODE_TAPE || p->strategy == KG_STRATEGY_CSR) {
     if ((rc = ws_alloc(p, &p->tape, tape_bytes, "tape c_e")) != KG_OK) return rc;
   }
+  // FP64 arithmetic: float pairs when G is within the pair range (u is checked per call)
+  if (p->dtype == KG_F32) {
+    p->arith = KG_ARITH_NATIVE;
+  } else if (p->arith != KG_ARITH_NATIVE) {
+    bool in_range = false;
+    if ((rc = pair_range_ok(p, static_cast<const double*>(p->data1), 12 * p->m, s, &in_range)) != KG_OK)
+      return rc;
+    if (!in_range && p->arith == KG_ARITH_PAIR)
+      return fail(KG_ERR_UNSUPPORTED, "TETENERGY PAIR arithmetic: G has entries outside "
+                                      "0 or [2^-60, 2^40) in magnitude");
+    p->arith = in_range ? KG_ARITH_PAIR : KG_ARITH_NATIVE;
+  }
+  if ((rc = tet_staged_setup(p)) != KG_OK) return rc;
   const int64_t n4 = 4 * p->m;
   const int* conn = static_cast<const int*>(p->data0);
   tet_validate_kernel<<<grid_for(n4, 256, 8), 256, 0, s>>>(conn, n4, (int)p->n, p->err);
@@ -300,41 +210,10 @@ kg_status tet_setup(kg_problem* p, cudaStream_t s) {
   return KG_OK;
 }
 
-template <typename T>
-static TetArgs<T> tet_args(kg_problem* p, const void* x, const void* seed, void* f) {
-  TetArgs<T> a{};
-  a.conn = static_cast<const int4*>(p->data0);
-  a.G = static_cast<const T*>(p->data1);
-  a.u = static_cast<const T*>(x);
-  a.ne = p->m;
-  a.nv = (int)p->n;
-  a.seed = static_cast<const T*>(seed);
-  a.tape = static_cast<T*>(p->tape);
-  a.fpart = p->fpart;
-  a.counter = p->counter;
-  a.f = static_cast<T*>(f);
-  a.err = p->err;
-  a.check = p->opt.check;
-  return a;
-}
-
-template <typename T>
-static kg_status tet_eval_t(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s) {
-  TetArgs<T> a = tet_args<T>(p, x, nullptr, f);
-  prof_begin(s, tape ? "tet_kernel<tape>" : "tet_kernel<eval>");
-  if (tape) tet_kernel<T, TET_TAPE><<<p->tet_grid, p->tet_block, 0, s>>>(a);
-  else tet_kernel<T, TET_EVAL><<<p->tet_grid, p->tet_block, 0, s>>>(a);
-  prof_end(s);
-  count_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "tet forward kernel");
-  if (tape) p->tape_valid = true;
-  return KG_OK;
-}
-
 kg_status tet_eval(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s) {
-  return p->dtype == KG_F64 ? tet_eval_t<double>(p, x, f, tape, s)
-                            : tet_eval_t<float>(p, x, f, tape, s);
+  kg_status rc = tet_staged(p, tape ? 2 : 0, x, f, nullptr, nullptr, s);
+  if (rc == KG_OK && tape) p->tape_valid = true;
+  return rc;
 }
 
 template <typename T>
@@ -369,7 +248,7 @@ template <typename T>
 static kg_status tet_grad_t(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
                             int accumulate, cudaStream_t s) {
   if (p->strategy == KG_STRATEGY_CSR) {
-    kg_status rc = tet_eval_t<T>(p, x, f, true, s);
+    kg_status rc = tet_eval(p, x, f, true, s);
     if (rc != KG_OK) return rc;
     return tet_scatter_t<T>(p, gx, seed, accumulate, s);
   }
@@ -379,14 +258,7 @@ static kg_status tet_grad_t(kg_problem* p, const void* x, void* f, void* gx, con
       return cuda_fail(e, "zero gu");
     count_launch();
   }
-  TetArgs<T> a = tet_args<T>(p, x, seed, f);
-  a.gu = static_cast<T*>(gx);
-  prof_begin(s, "tet_kernel<grad>");
-  tet_kernel<T, TET_GRAD><<<p->tet_grid, p->tet_block, 0, s>>>(a);
-  prof_end(s);
-  count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "tet fused value-and-grad kernel");
-  return KG_OK;
+  return tet_staged(p, 1, x, f, gx, seed, s);
 }
 
 kg_status tet_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,

@@ -1,0 +1,421 @@
+// Tet-mesh energy kernels with shared-memory staging of the element data.
+//
+// Each CTA walks tiles of 256 elements (tile = blockIdx.x, + gridDim.x, ...).
+// Thread 0 streams each tile's connectivity (int4 per element) and G_e
+// (12 values per element) into a two-stage shared-memory ring with TMA bulk
+// copies (cp.async.bulk, mbarrier transaction counts); warps release a stage
+// through an "empty" mbarrier and thread 0 refills it.  Thread i of the CTA
+// handles element i of the tile: gathers u_e (4 reads through the index map,
+// mostly L2 hits), computes g_e = G_e u_e, f_e = log1p(|g_e|^2) and, in the
+// reverse modes, c_e = G_e^T (2 fbar g_e / (1 + |g_e|^2)), which it either
+// scatter-adds into gu (FP64/FP32 atomics) or stores to the tape.
+//
+// Arithmetic: FP32 for FP32 problems; for FP64 problems either native FP64
+// or float pairs (kg_pair.cuh) with the results converted back to double for
+// the atomics / tape (KG_ARITH_PAIR: GB300's FP64 units are ~60x slower than
+// its FP32 units).  All waits are bounded.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+#include <string>
+
+#include "kg_device.cuh"
+#include "kg_internal.h"
+#include "kg_pair.cuh"
+
+namespace kg {
+
+constexpr int TS_THREADS = 256;  // threads per CTA == elements per tile
+constexpr int TS_WARPS = TS_THREADS / 32;
+constexpr int TS_STAGES = 2;
+
+enum { TS_EVAL = 0, TS_GRAD = 1, TS_TAPE = 2 };
+
+template <typename T>
+struct TsArgs {
+  const int4* conn;
+  const T* G;
+  const T* u;
+  int64_t ne;
+  int nv;
+  const T* seed;
+  T* gu;
+  T* tape;
+  double* fpart;
+  unsigned* counter;
+  T* f;
+  unsigned* err;
+  int check;
+  const float4* logtab;  // PAIR: 256 entries
+  LogConsts K;
+};
+
+__device__ __forceinline__ Acc shfl_xor_acc2(Acc a, int o) {
+  Acc b;
+  b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
+  b.l = __shfl_xor_sync(0xffffffffu, a.l, o);
+  return b;
+}
+
+template <typename T>
+__device__ __forceinline__ T log1p_nat(T v) {
+  if constexpr (sizeof(T) == 8) return log1p(v);
+  else return log1pf(v);
+}
+
+// One element in native arithmetic (T = float or double).
+template <typename T, int MODE>
+__device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ Gs,
+                                            const T* __restrict__ u, T fb, T& facc, T* gu,
+                                            T* tape_e) {
+  T G[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) G[i] = Gs[i];
+  const T u0 = __ldg(u + c.x), u1 = __ldg(u + c.y), u2 = __ldg(u + c.z), u3 = __ldg(u + c.w);
+  const T g0 = G[0] * u0 + G[1] * u1 + G[2] * u2 + G[3] * u3;
+  const T g1 = G[4] * u0 + G[5] * u1 + G[6] * u2 + G[7] * u3;
+  const T g2 = G[8] * u0 + G[9] * u1 + G[10] * u2 + G[11] * u3;
+  const T s = g0 * g0 + g1 * g1 + g2 * g2;
+  facc += log1p_nat(s);
+  if constexpr (MODE != TS_EVAL) {
+    const T w = T(2) * fb / (T(1) + s);
+    const T w0 = w * g0, w1 = w * g1, w2 = w * g2;
+    const T c0 = G[0] * w0 + G[4] * w1 + G[8] * w2;
+    const T c1 = G[1] * w0 + G[5] * w1 + G[9] * w2;
+    const T c2 = G[2] * w0 + G[6] * w1 + G[10] * w2;
+    const T c3 = G[3] * w0 + G[7] * w1 + G[11] * w2;
+    if constexpr (MODE == TS_GRAD) {
+      atomicAdd(gu + c.x, c0);
+      atomicAdd(gu + c.y, c1);
+      atomicAdd(gu + c.z, c2);
+      atomicAdd(gu + c.w, c3);
+    } else {
+      tape_e[0] = c0;
+      tape_e[1] = c1;
+      tape_e[2] = c2;
+      tape_e[3] = c3;
+    }
+  }
+}
+
+// One element in float-pair arithmetic (FP64 data).
+template <int MODE>
+__device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict__ Gs,
+                                          const double* __restrict__ u, Pair fb2,
+                                          const float4* __restrict__ tab, const LogConsts& K,
+                                          Acc& facc, double* gu, double* tape_e, bool& bad) {
+  Pair G[12];
+#pragma unroll
+  for (int i = 0; i < 12; i += 2) {
+    const double2 v = *reinterpret_cast<const double2*>(Gs + i);
+    G[i] = split_f64(v.x);
+    G[i + 1] = split_f64(v.y);
+  }
+  const double ud[4] = {__ldg(u + c.x), __ldg(u + c.y), __ldg(u + c.z), __ldg(u + c.w)};
+  Pair U[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    bad |= !pair_in_range(ud[k]);
+    U[k] = split_f64(ud[k]);
+  }
+  Pair g[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    Acc a = acc_zero();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, U[k].h, U[k].l);
+    g[r] = acc_pair(a);
+  }
+  Acc sa = acc_zero();
+#pragma unroll
+  for (int r = 0; r < 3; ++r) acc_fma(sa, g[r].h, g[r].l, g[r].h, g[r].l);
+  const Pair s = acc_pair(sa);
+  Pair t;
+  const Pair lf = pair_log1p(s, tab, K, t);
+  facc = acc_add(facc, Acc{lf.h, lf.l});
+  if constexpr (MODE != TS_EVAL) {
+    const Pair w = pair_mul(fb2, pair_recip(t));
+    Pair wg[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) wg[r] = pair_mul(w, g[r]);
+    double cd[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Acc a = acc_zero();
+#pragma unroll
+      for (int r = 0; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, wg[r].h, wg[r].l);
+      cd[k] = pair_to_double_fast(acc_pair(a));
+    }
+    if constexpr (MODE == TS_GRAD) {
+      atomicAdd(gu + c.x, cd[0]);
+      atomicAdd(gu + c.y, cd[1]);
+      atomicAdd(gu + c.z, cd[2]);
+      atomicAdd(gu + c.w, cd[3]);
+    } else {
+      reinterpret_cast<double2*>(tape_e)[0] = make_double2(cd[0], cd[1]);
+      reinterpret_cast<double2*>(tape_e)[1] = make_double2(cd[2], cd[3]);
+    }
+  }
+}
+
+template <typename T, bool PAIR, int MODE>
+__global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr uint32_t kConnBytes = TS_THREADS * 16u;
+  constexpr uint32_t kGBytes = TS_THREADS * 12u * sizeof(T);
+  constexpr uint32_t kStage = kConnBytes + kGBytes;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + TS_STAGES * kStage);
+  uint64_t* empty = full + TS_STAGES;
+  float4* tab = reinterpret_cast<float4*>(empty + TS_STAGES);  // PAIR only
+  double* red = reinterpret_cast<double*>(tab + (PAIR ? kLogTableSize : 0));
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(red + 2 * TS_WARPS);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t ntiles = (a.ne + TS_THREADS - 1) / TS_THREADS;
+  const int64_t my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+
+  if (tid == 0) {
+    for (int s = 0; s < TS_STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], TS_WARPS);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  if constexpr (PAIR) {
+    for (int i = tid; i < kLogTableSize; i += TS_THREADS) tab[i] = a.logtab[i];
+  }
+  __syncthreads();
+
+  auto issue = [&](int64_t i, int s) {  // tile i of this CTA into stage s
+    const int64_t tile = blockIdx.x + i * (int64_t)gridDim.x;
+    const int64_t e0 = tile * TS_THREADS;
+    const int64_t cnt = a.ne - e0 < TS_THREADS ? a.ne - e0 : TS_THREADS;
+    unsigned char* st = smem + s * kStage;
+    const uint32_t cb = (uint32_t)cnt * 16u, gb = (uint32_t)cnt * 12u * (uint32_t)sizeof(T);
+    mbar_arrive_expect_tx(&full[s], cb + gb);
+    tma_load_1d(st, a.conn + e0, cb, &full[s]);
+    tma_load_1d(st + kConnBytes, a.G + e0 * 12, gb, &full[s]);
+  };
+  int64_t issued = 0;
+  if (tid == 0) {
+    for (int64_t i = 0; i < TS_STAGES && i < my_tiles; ++i) {
+      issue(i, (int)i);
+      ++issued;
+    }
+  }
+
+  T facc_n = T(0);
+  Acc facc_p = acc_zero();
+  bool bad = false;
+  const T fb = MODE == TS_GRAD ? load_seed(a.seed) : T(1);
+  Pair fb2{2.0f, 0.0f};
+  if constexpr (PAIR) {
+    if (MODE == TS_GRAD) {
+      bad |= !pair_in_range(2.0 * (double)fb);
+      fb2 = split_f64(2.0 * (double)fb);
+    }
+  }
+
+  for (int64_t i = 0; i < my_tiles; ++i) {
+    const int s = (int)(i % TS_STAGES);
+    const uint32_t par = (uint32_t)((i / TS_STAGES) & 1);
+    bool ok = !*abort_flag;
+    if (ok && !mbar_wait_bounded(&full[s], par)) {
+      set_error(a.err, ERRBIT_TIMEOUT);
+      *abort_flag = 1;
+      ok = false;
+    }
+    const int64_t e = (blockIdx.x + i * (int64_t)gridDim.x) * TS_THREADS + tid;
+    if (ok && e < a.ne) {
+      const unsigned char* st = smem + s * kStage;
+      const int4 c = reinterpret_cast<const int4*>(st)[tid];
+      const T* Gs = reinterpret_cast<const T*>(st + kConnBytes) + tid * 12;
+      bool inb = true;
+      if (a.check) {
+        inb = (unsigned)c.x < (unsigned)a.nv && (unsigned)c.y < (unsigned)a.nv &&
+              (unsigned)c.z < (unsigned)a.nv && (unsigned)c.w < (unsigned)a.nv;
+        if (!inb) set_error(a.err, ERRBIT_BOUNDS);
+      }
+      if (inb) {
+        if constexpr (PAIR) {
+          elem_pair<MODE>(c, reinterpret_cast<const double*>(Gs), reinterpret_cast<const double*>(a.u),
+                          fb2, tab, a.K, facc_p, reinterpret_cast<double*>(a.gu),
+                          reinterpret_cast<double*>(a.tape) + e * 4, bad);
+          if ((i & 31) == 31) acc_renorm(facc_p);
+        } else {
+          elem_native<T, MODE>(c, Gs, a.u, fb, facc_n, a.gu, a.tape + e * 4);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[s]);
+    if (tid == 0 && i + TS_STAGES < my_tiles && !*abort_flag) {
+      if (!mbar_wait_bounded(&empty[s], par)) {
+        set_error(a.err, ERRBIT_TIMEOUT);
+        *abort_flag = 1;
+      } else {
+        issue(i + TS_STAGES, s);
+        ++issued;
+      }
+    }
+    __syncwarp();
+  }
+  if (tid == 0) {  // no copy into this CTA's shared memory may still be in flight
+    for (int s = 0; s < TS_STAGES; ++s) {
+      int64_t last = -1;
+      for (int64_t j = issued - 1; j >= 0 && j >= issued - TS_STAGES; --j)
+        if ((int)(j % TS_STAGES) == s) last = j;
+      if (last >= 0) mbar_wait_bounded(&full[s], (uint32_t)((last / TS_STAGES) & 1));
+    }
+  }
+  if (bad) set_error(a.err, ERRBIT_RANGE);
+
+  // CTA sum of f (deterministic), then the last CTA sums the CTA partials.
+  double fcta;
+  if constexpr (PAIR) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) facc_p = acc_add(facc_p, shfl_xor_acc2(facc_p, o));
+    Acc* ra = reinterpret_cast<Acc*>(red);
+    if (lane == 0) ra[warp] = facc_p;
+    __syncthreads();
+    Acc tot = acc_zero();
+    for (int w = 0; w < TS_WARPS; ++w) tot = acc_add(tot, ra[w]);
+    fcta = acc_to_double(tot);
+    __syncthreads();
+  } else {
+    fcta = block_sum((double)facc_n, red);
+  }
+  finish_sum<T>(fcta, a.fpart, a.counter, a.f, 0, red);
+}
+
+// ---------------------------------------------------------------- host ----
+static float4* g_logtab[64] = {nullptr};
+static std::mutex g_logtab_mu;
+
+static void split_ld(long double v, float& h, float& l) {
+  h = (float)v;
+  l = (float)(v - (long double)h);
+}
+
+static LogConsts log_consts() {
+  LogConsts K;
+  split_ld(logl(2.0L), K.ln2_h, K.ln2_l);
+  split_ld(1.0L / 3.0L, K.third_h, K.third_l);
+  return K;
+}
+
+// The 256-entry table (log c_k, 1/c_k) for c_k = 1 + k/256, computed on the
+// host in extended precision and uploaded once per device (kept until exit).
+static kg_status logtab_for_device(const float4** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= 64) return fail(KG_ERR_UNSUPPORTED, "device index >= 64");
+  std::lock_guard<std::mutex> lk(g_logtab_mu);
+  if (!g_logtab[dev]) {
+    float4 h[kLogTableSize];
+    for (int k = 0; k < kLogTableSize; ++k) {
+      const long double c = 1.0L + (long double)k / kLogTableSize;
+      split_ld(logl(c), h[k].x, h[k].y);
+      split_ld(1.0L / c, h[k].z, h[k].w);
+    }
+    void* d = nullptr;
+    if ((e = dev_alloc(&d, sizeof(h))) != cudaSuccess)
+      return fail(KG_ERR_OOM, "log table allocation failed");
+    if ((e = cudaMemcpy(d, h, sizeof(h), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(e, "log table upload");
+    }
+    g_logtab[dev] = static_cast<float4*>(d);
+  }
+  *out = g_logtab[dev];
+  return KG_OK;
+}
+
+template <typename T, bool PAIR>
+static size_t ts_smem() {
+  return (size_t)TS_STAGES * (TS_THREADS * 16 + TS_THREADS * 12 * sizeof(T)) +
+         2 * TS_STAGES * sizeof(uint64_t) + (PAIR ? kLogTableSize * sizeof(float4) : 0) +
+         2 * TS_WARPS * sizeof(double) + 16;
+}
+
+int tet_staged_grid(const kg_problem* p) {
+  const int64_t ntiles = (p->m + TS_THREADS - 1) / TS_THREADS;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 3));
+}
+
+kg_status tet_staged_setup(kg_problem* p) {
+  if (p->dtype == KG_F64 && p->arith == KG_ARITH_PAIR) {
+    const float4* t = nullptr;
+    kg_status rc = logtab_for_device(&t);
+    if (rc != KG_OK) return rc;
+  }
+  return KG_OK;
+}
+
+template <typename T, bool PAIR, int MODE>
+static cudaError_t launch_ts(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
+  auto kern = tet_staged_kernel<T, PAIR, MODE>;
+  const size_t smem = ts_smem<T, PAIR>();
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<p->tet_grid, TS_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t dispatch_ts(const kg_problem* p, int mode, const TsArgs<T>& a, cudaStream_t s) {
+  const bool pair = sizeof(T) == 8 && p->arith == KG_ARITH_PAIR;
+  if (pair) {
+    if constexpr (sizeof(T) == 8) {
+      if (mode == TS_EVAL) return launch_ts<T, true, TS_EVAL>(p, a, s);
+      if (mode == TS_GRAD) return launch_ts<T, true, TS_GRAD>(p, a, s);
+      return launch_ts<T, true, TS_TAPE>(p, a, s);
+    }
+  }
+  if (mode == TS_EVAL) return launch_ts<T, false, TS_EVAL>(p, a, s);
+  if (mode == TS_GRAD) return launch_ts<T, false, TS_GRAD>(p, a, s);
+  return launch_ts<T, false, TS_TAPE>(p, a, s);
+}
+
+template <typename T>
+static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, void* gx,
+                              const void* seed, cudaStream_t s) {
+  TsArgs<T> a{};
+  a.conn = static_cast<const int4*>(p->data0);
+  a.G = static_cast<const T*>(p->data1);
+  a.u = static_cast<const T*>(x);
+  a.ne = p->m;
+  a.nv = (int)p->n;
+  a.seed = static_cast<const T*>(seed);
+  a.gu = static_cast<T*>(gx);
+  a.tape = static_cast<T*>(p->tape);
+  a.fpart = p->fpart;
+  a.counter = p->counter;
+  a.f = static_cast<T*>(f);
+  a.err = p->err;
+  a.check = p->opt.check;
+  a.K = log_consts();
+  if (sizeof(T) == 8 && p->arith == KG_ARITH_PAIR) {
+    kg_status rc = logtab_for_device(&a.logtab);
+    if (rc != KG_OK) return rc;
+  }
+  static const char* names[3] = {"tet_staged_kernel<eval>", "tet_staged_kernel<grad>",
+                                 "tet_staged_kernel<tape>"};
+  prof_begin(s, names[mode]);
+  cudaError_t e = dispatch_ts<T>(p, mode, a, s);
+  prof_end(s);
+  count_launch();
+  return e == cudaSuccess ? KG_OK : cuda_fail(e, names[mode]);
+}
+
+kg_status tet_staged(kg_problem* p, int mode, const void* x, void* f, void* gx, const void* seed,
+                     cudaStream_t s) {
+  return p->dtype == KG_F64 ? tet_staged_t<double>(p, mode, x, f, gx, seed, s)
+                            : tet_staged_t<float>(p, mode, x, f, gx, seed, s);
+}
+
+}  // namespace kg

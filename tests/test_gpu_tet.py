@@ -97,15 +97,21 @@ def test_csr_is_bitwise_reproducible_and_close_to_atomic(api):
     assert rel_l2(ga.cpu().numpy(), g1.cpu().numpy()) <= TOL["f64"]
 
 
-def test_linear_field_interior_gradient_vanishes(api):
+@pytest.mark.parametrize("arith", ["native", "pair"])
+def test_linear_field_interior_gradient_vanishes(api, arith):
+    # P1 reproduces linear fields: g_e = a on every element, and the incident
+    # gradients cancel at interior vertices (equal tet volumes).  The residual is
+    # rounding: ~1e-15 for FP64 instructions, ~2^-46 of the O(1) terms for pairs.
     mesh = W.tet_mesh(6, perm_seed=2)
     a = np.array([0.2, -0.4, 0.1])
-    p = _problem(api, mesh, torch.float64)
+    p = _problem(api, mesh, torch.float64, arith=arith)
     f, g = p.grad(torch.tensor(W.linear_field(mesh, a), device="cuda"))
+    g = g.cpu().numpy()
     gi = np.rint(mesh.coords).astype(int)
     interior = np.all((gi > 0) & (gi < 6), axis=1)
     assert rel_scalar(f.item(), mesh.ne * np.log1p(a @ a)) <= TOL["f64"]
-    assert np.max(np.abs(g.cpu().numpy()[interior])) < 1e-13
+    bound = 1e-13 if arith == "native" else TOL["f64"] * np.max(np.abs(g))
+    assert np.max(np.abs(g[interior])) < bound
 
 
 def test_full_size_100_cubed_f64(api):
@@ -146,3 +152,58 @@ def test_checked_kernels_flag_connectivity_changed_after_create(api):
         p.sync()
     assert ei.value.status == L.KG_ERR_BOUNDS
     p.sync()  # the sticky word was cleared by the read
+
+
+@pytest.mark.parametrize("arith", ["pair", "native"])
+@pytest.mark.parametrize("strategy", ["atomic", "csr"])
+def test_pair_and_native_match_oracle_jittered(api, arith, strategy):
+    mesh = W.tet_mesh(18, jitter_seed=2, perm_seed=5)
+    u = np.random.default_rng(21).uniform(-1, 1, mesh.nv)
+    f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u, fbar=1.3)
+    p = _problem(api, mesh, torch.float64, strategy=strategy, arith=arith, mode="tape")
+    assert p.config[2] == arith
+    ut = torch.tensor(u, device="cuda")
+    seed = torch.tensor(1.3, dtype=torch.float64, device="cuda")
+    f, g = p.grad(ut, seed=seed)
+    ft = p.eval_tape(ut)
+    gt = p.grad_from_tape(seed=seed)
+    p.sync()
+    assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+    assert rel_scalar(ft.item(), f_ref) <= TOL["f64"]
+    assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+    assert rel_l2(gt.cpu().numpy(), g_ref) <= TOL["f64"]
+
+
+def test_pair_default_and_range_rules(api):
+    from paper_2507_13204_gb300 import _lib as L
+    mesh = W.tet_mesh(5, jitter_seed=2)
+    p = _problem(api, mesh, torch.float64)
+    assert p.config == ("atomic", "tape", "pair")
+    u = np.random.default_rng(1).uniform(-1, 1, mesh.nv)
+    u[3] = 1e200  # outside the pair range: reported, not silently wrong
+    p.grad(torch.tensor(u, device="cuda"))
+    with pytest.raises(L.KGError) as ei:
+        p.sync()
+    assert ei.value.status == L.KG_ERR_RANGE
+    G = mesh.G.copy()
+    G[0, 0] = 1e-80  # G outside the range: AUTO picks native FP64, PAIR is refused
+    q = api.TetEnergy(torch.tensor(mesh.conn, device="cuda"), torch.tensor(G, device="cuda"), mesh.nv)
+    assert q.config[2] == "native"
+    with pytest.raises(L.KGError) as ei:
+        api.TetEnergy(torch.tensor(mesh.conn, device="cuda"), torch.tensor(G, device="cuda"),
+                      mesh.nv, arith="pair")
+    assert ei.value.status == L.KG_ERR_UNSUPPORTED
+
+
+def test_ragged_tiles_and_tiny_meshes(api):
+    # element counts that are not multiples of the 256-element tile
+    for a, b, c in [(1, 1, 1), (1, 1, 7), (3, 5, 2), (11, 1, 3)]:
+        mesh = W.tet_mesh(a, b, c, jitter_seed=None, perm_seed=a + b + c)
+        u = np.random.default_rng(a * b * c).uniform(-1, 1, mesh.nv)
+        f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
+        for arith in ("pair", "native"):
+            p = _problem(api, mesh, torch.float64, arith=arith)
+            f, g = p.grad(torch.tensor(u, device="cuda"))
+            p.sync()
+            assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+            assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
