@@ -202,6 +202,24 @@ kg_status kg_grad_batched(kg_batch *b, const void *const *x, void *const *f, voi
 kg_status kg_grad_batched_loop(kg_batch *b, const void *const *x, void *const *f,
                                void *const *gx, kg_stream s);
 
+/* Allocation-free value and gradient of f(x) = ||A x||^2 in FP64 (the paper
+ * has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory, e.g. code under a memory manager that owns the
+ * whole device heap, or a loop that must never enter the allocator).
+ *   A   m x n, row-major, device; x (n) device; f (device scalar, nullable);
+ *   gx  (n) device, overwritten with the gradient (output adjoint 1).
+ *   Limits: FP64 only, 1 <= m < 2^31, 1 <= n <= 12288; larger sizes return
+ *   KG_ERR_INVALID_ARG with a message.  No handle, no cudaMalloc/cudaFree.
+ * Scratch: a fixed 16 MiB array compiled into libkg.so, present on every GPU
+ * that loads the library until the process exits.  The first call on a
+ * device looks up its address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call
+ * shares the array and leaves its contents behind (the kernels overwrite
+ * what they read, so nothing has to be cleared); calls that overlap on the
+ * GPU race on it and must be serialised by the caller.  Asynchronous on `s`. */
+kg_status kg_quadform_grad_noalloc(const double *A, int64_t m, int64_t n, const double *x,
+                                   double *f, double *gx, kg_stream s);
+
 /* Synchronises the problem's last stream and reads its sticky device error
  * word (cleared by the read): KG_ERR_BOUNDS, KG_ERR_TIMEOUT, KG_ERR_RANGE or
  * KG_OK. */

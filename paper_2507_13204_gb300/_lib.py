@@ -29,7 +29,7 @@ EXPORTS = ["kg_options_default", "kg_create", "kg_eval", "kg_grad", "kg_eval_tap
            "kg_grad_from_tape", "kg_grad_host", "kg_batch_create", "kg_grad_batched",
            "kg_grad_batched_loop", "kg_sync", "kg_batch_sync", "kg_last_error",
            "kg_get_config", "kg_workspace_bytes", "kg_last_launch_count", "kg_profile_enable", "kg_profile_read",
-           "kg_destroy", "kg_batch_destroy"]
+           "kg_quadform_grad_noalloc", "kg_destroy", "kg_batch_destroy"]
 
 
 class kg_options(ctypes.Structure):
@@ -83,6 +83,7 @@ def lib():
                 "kg_profile_enable": (st, [i]),
                 "kg_profile_read": (st, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_char_p)]),
+                "kg_quadform_grad_noalloc": (st, [vp, ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp]),
                 "kg_destroy": (None, [vp]),
                 "kg_batch_destroy": (None, [vp]),
             }

@@ -85,6 +85,10 @@ kg_status qf_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status qf_grad(kg_problem* p, const void* x, void* f, void* gx, void* gA, const void* seed,
                   int accumulate, cudaStream_t s);
 
+kg_status qf_native_fused_on_scratch(const double* A, int64_t m, int64_t n, const double* x,
+                                     double* f, double* gx, double* scratch,
+                                     size_t scratch_doubles, cudaStream_t s);
+
 // float-pair dense kernels (quadform_pair.cu)
 bool qf_pair_supported(const kg_problem* p);
 kg_status pair_range_ok(kg_problem* p, const double* data, int64_t count, cudaStream_t s, bool* ok);

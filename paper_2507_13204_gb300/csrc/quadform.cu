@@ -478,6 +478,44 @@ static kg_status qf_grad_t(kg_problem* p, const void* x, void* f, void* gx, void
   return KG_OK;
 }
 
+// Native FP64 fused value-and-gradient with every workspace taken from
+// `scratch` (partials: grid * n doubles, then grid f partials).  The fused
+// kernel writes all of them before the reduce kernel reads them, so the
+// scratch needs no clearing.  KG_ERR_INVALID_ARG if it is too small.
+kg_status qf_native_fused_on_scratch(const double* A, int64_t m, int64_t n, const double* x,
+                                     double* f, double* gx, double* scratch,
+                                     size_t scratch_doubles, cudaStream_t s) {
+  const int var = pick_variant(n, 0);
+  if (var < 0) return fail(KG_ERR_INVALID_ARG, "n must be <= 12288");
+  const QfVariant& v = kVariants[var];
+  const int nteams = v.block / v.team;
+  const int resident = v.block >= 512 ? 1 : 2;
+  const int64_t target = (int64_t)num_sms() * resident;
+  const int64_t rows = std::max<int64_t>(nteams, (m + target - 1) / target);
+  const int grid = (int)((m + rows - 1) / rows);
+  const size_t need = (size_t)grid * (size_t)n + (size_t)grid;
+  if (need > scratch_doubles)
+    return fail(KG_ERR_INVALID_ARG, "problem needs " + std::to_string(need) +
+                                        " scratch doubles, more than the " +
+                                        std::to_string(scratch_doubles) + " available");
+  QfArgs<double> a{};
+  a.A = A;
+  a.x = x;
+  a.m = m;
+  a.n = (int)n;
+  a.cpt = (int)((n + v.team - 1) / v.team);
+  a.rows_per_cta = (int)rows;
+  a.partials = scratch;
+  a.fpart = scratch + (size_t)grid * n;
+  cudaError_t e = launch_team<double, QF_FUSED>(var, dim3(grid), s, a);
+  if (e != cudaSuccess) return cuda_fail(e, "qf fused kernel");
+  qf_reduce_kernel<double><<<(int)((n + 31) / 32), 512, 0, s>>>(scratch, grid, (int)n, a.fpart, grid,
+                                                               gx, f, 0);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "qf reduce kernel");
+  return KG_OK;
+}
+
 kg_status qf_grad(kg_problem* p, const void* x, void* f, void* gx, void* gA, const void* seed,
                   int accumulate, cudaStream_t s) {
   if (p->arith == KG_ARITH_PAIR) {
