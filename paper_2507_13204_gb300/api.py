@@ -150,9 +150,9 @@ class Laplace1D(Problem):
 class Batch:
     """Many problems differentiated by one persistent launch (graph-replayed)."""
 
-    def __init__(self, problems, block=0, tile=0, stream=None):
+    def __init__(self, problems, arith="auto", stream=None):
         self.problems = list(problems)
-        opt = L.options(dtype=_DT[self.problems[0].dtype], block=block, tile=tile)
+        opt = L.options(dtype=_DT[self.problems[0].dtype], arith=ARITHS[arith])
         self.handle = L.kg_batch_create([p.handle for p in self.problems], opt, stream)
 
     def grad(self, xs, fs, gxs, stream=None):

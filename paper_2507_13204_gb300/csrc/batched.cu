@@ -1,9 +1,924 @@
-// placeholder, replaced by the batched persistent kernel
+// Batched value-and-gradient of many independent problems in ONE persistent
+// kernel launch, replayed from a CUDA graph (the paper's Sec. 5 second
+// restriction: the generated gradient doubles the kernel launches and host
+// synchronisation points; here a whole batch of gradients is one launch).
+//
+// Work: every instance is cut into tiles -- row tiles for the dense quadratic
+// form, element tiles for the tet energy -- and the (instance, tile) items are
+// sorted longest-first into a device work table.  Each CTA of the persistent
+// grid claims items from a device queue head (one atomicAdd per item) until
+// the table is exhausted.
+//   dense tile:  rows [r0, r0 + R): y_i by a row team (a warp for n <= 256,
+//                the CTA otherwise), ybar_i = 2 y_i, private xbar partial of
+//                the tile written to the instance's partial buffer;
+//   tet tile:    elements [e0, e0 + T): f_e and the atomic scatter of c_e
+//                into gu (zeroed by a small kernel earlier in the graph).
+// The CTA that finishes an instance's last tile (a per-instance arrival
+// counter; nobody waits) sums the instance's partials in tile order into gx
+// and f, and resets the counter.  The last CTA to leave resets the queue head,
+// so the graph can be replayed as is.
+//
+// Tile sizes R and T are chosen per (kind, size bucket) by an autotuner that
+// times candidates on the instances of the batch at kg_batch_create and keeps
+// the choices in a JSON cache keyed by GPU name, kind, dtype and bucket.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <new>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include <sys/stat.h>
+
+#include "kg_device.cuh"
 #include "kg_internal.h"
-extern "C" {
-kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count, const kg_options* opt, kg_stream s) { return KG_ERR_UNSUPPORTED; }
-kg_status kg_grad_batched(kg_batch* b, const void* const* x, void* const* f, void* const* gx, kg_stream s) { return KG_ERR_UNSUPPORTED; }
-kg_status kg_grad_batched_loop(kg_batch* b, const void* const* x, void* const* f, void* const* gx, kg_stream s) { return KG_ERR_UNSUPPORTED; }
-kg_status kg_batch_sync(kg_batch* b) { return KG_ERR_UNSUPPORTED; }
-void kg_batch_destroy(kg_batch* b) {}
+#include "kg_pair.cuh"
+#include "kg_tet_elem.cuh"
+
+namespace kg {
+
+enum { BK_DENSE = 1, BK_TET = 2 };
+constexpr int BT = 256;   // threads per CTA
+constexpr int BW = BT / 32;
+constexpr int B_CPT = 8;  // dense: columns per team thread (n <= 8 * team)
+constexpr int B_MAXN = 2048;
+
+struct BInst {
+  int kind;
+  int n;      // dense: columns; tet: vertices
+  int64_t m;  // dense: rows; tet: elements
+  int ntiles;
+  int team;   // dense: 32 or 256
+  const void* d0;
+  const void* d1;
+  const void* x;
+  void* f;
+  void* gx;
+  void* partials;  // dense: [ntiles][n]  (pair: Acc; native: T)
+  double* fpart;   // [ntiles]
+  unsigned* done;
+};
+
+struct BItem {
+  int inst, tile;
+  int64_t start;
+  int count;
+};
+
+struct BArgs {
+  const BInst* insts;
+  const BItem* items;
+  int nitems;
+  unsigned* head;  // [0] queue head, [1] CTAs that left
+  unsigned* err;
+  const float4* logtab;
+  LogConsts K;
+};
+
+// ------------------------------------------------------------- device ----
+template <bool PAIR, typename T>
+__device__ __forceinline__ void b_split(T v, float& h, float& l) {
+  if constexpr (PAIR) {
+    const Pair p = split_f64((double)v);
+    h = p.h;
+    l = p.l;
+  } else {
+    h = 0.f;
+    l = 0.f;
+  }
 }
+
+// Rows [w.start, w.start + w.count) of a dense instance; returns the tile's f.
+template <typename T, bool PAIR, int TEAM>
+__device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp, double* red,
+                             bool& bad) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = I.n;
+  const T* __restrict__ A = static_cast<const T*>(I.d0);
+  const T* __restrict__ x = static_cast<const T*>(I.x);
+  constexpr int NT = BT / TEAM;
+  const int lt = tid % TEAM, team = tid / TEAM;
+  float xh[B_CPT], xl[B_CPT];
+  T xv[B_CPT];
+  Acc xbp[B_CPT];
+  T xbn[B_CPT];
+#pragma unroll
+  for (int k = 0; k < B_CPT; ++k) {
+    const int j = lt + k * TEAM;
+    xv[k] = j < n ? x[j] : T(0);
+    if constexpr (PAIR) {
+      bad |= !pair_in_range((double)xv[k]);
+      b_split<PAIR>(xv[k], xh[k], xl[k]);
+    }
+    xbp[k] = acc_zero();
+    xbn[k] = T(0);
+  }
+  Acc fp = acc_zero();
+  double fn = 0.0;
+  const int64_t r1 = w.start + w.count;
+  const int iters = (w.count + NT - 1) / NT;
+  for (int itr = 0; itr < iters; ++itr) {
+    const int64_t r = w.start + (int64_t)itr * NT + team;
+    const bool valid = r < r1;
+    const T* Ar = A + (valid ? r : w.start) * (int64_t)n;
+    float ah[B_CPT], al[B_CPT];
+    T av[B_CPT];
+#pragma unroll
+    for (int k = 0; k < B_CPT; ++k) {
+      const int j = lt + k * TEAM;
+      av[k] = (valid && j < n) ? __ldcs(Ar + j) : T(0);
+      if constexpr (PAIR) b_split<PAIR>(av[k], ah[k], al[k]);
+    }
+    if constexpr (PAIR) {
+      Acc y0 = acc_zero(), y1 = acc_zero();
+#pragma unroll
+      for (int k = 0; k < B_CPT; k += 2) {
+        acc_fma(y0, ah[k], al[k], xh[k], xl[k]);
+        acc_fma(y1, ah[k + 1], al[k + 1], xh[k + 1], xl[k + 1]);
+      }
+      Acc yv = acc_add(y0, y1);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) yv = acc_add(yv, shfl_xor_acc2(yv, o));
+      if constexpr (TEAM > 32) {
+        Acc* ra = reinterpret_cast<Acc*>(red) + (itr & 1) * BW;
+        if (lane == 0) ra[warp] = yv;
+        __syncthreads();
+        yv = ra[0];
+#pragma unroll
+        for (int q = 1; q < BW; ++q) yv = acc_add(yv, ra[q]);
+      }
+      if (valid) {
+        const Pair y = acc_pair(yv);
+        const Pair y2 = pair_mul(y, y);
+        fp = acc_add(fp, Acc{y2.h, y2.l});
+        const Pair yb{2.0f * y.h, 2.0f * y.l};  // exact
+#pragma unroll
+        for (int k = 0; k < B_CPT; ++k) acc_fma(xbp[k], ah[k], al[k], yb.h, yb.l);
+        if ((itr & 15) == 15) {
+#pragma unroll
+          for (int k = 0; k < B_CPT; ++k) acc_renorm(xbp[k]);
+        }
+      }
+    } else {
+      T d = T(0);
+#pragma unroll
+      for (int k = 0; k < B_CPT; ++k) d = fma(av[k], xv[k], d);
+      d = warp_sum(d);
+      if constexpr (TEAM > 32) {
+        T* rt = reinterpret_cast<T*>(red) + (itr & 1) * BW;
+        if (lane == 0) rt[warp] = d;
+        __syncthreads();
+        d = rt[0];
+#pragma unroll
+        for (int q = 1; q < BW; ++q) d += rt[q];
+      }
+      if (valid) {
+        fn += (double)d * (double)d;
+        const T yb = T(2) * d;
+#pragma unroll
+        for (int k = 0; k < B_CPT; ++k) xbn[k] = fma(yb, av[k], xbn[k]);
+      }
+    }
+  }
+  // combine the teams' partials in team order and store the tile's partial
+  __syncthreads();
+  if constexpr (PAIR) {
+    Acc* out = static_cast<Acc*>(I.partials) + (int64_t)w.tile * n;
+    if constexpr (NT == 1) {
+#pragma unroll
+      for (int k = 0; k < B_CPT; ++k) {
+        const int j = lt + k * TEAM;
+        if (j < n) out[j] = xbp[k];
+      }
+    } else {
+      Acc* ws = reinterpret_cast<Acc*>(wsp);  // [NT][TEAM * B_CPT]
+#pragma unroll
+      for (int k = 0; k < B_CPT; ++k) ws[team * TEAM * B_CPT + lt + k * TEAM] = xbp[k];
+      __syncthreads();
+      for (int j = tid; j < n; j += BT) {
+        Acc s = ws[j];
+        for (int t2 = 1; t2 < NT; ++t2) s = acc_add(s, ws[t2 * TEAM * B_CPT + j]);
+        out[j] = s;
+      }
+    }
+    // f of the tile: team leaders in team order
+    Acc* ra = reinterpret_cast<Acc*>(red);
+    __syncthreads();
+    if (lt == 0) ra[team] = fp;
+    __syncthreads();
+    Acc tot = ra[0];
+    for (int t2 = 1; t2 < NT; ++t2) tot = acc_add(tot, ra[t2]);
+    __syncthreads();
+    return acc_to_double(tot);
+  } else {
+    T* out = static_cast<T*>(I.partials) + (int64_t)w.tile * n;
+    if constexpr (NT == 1) {
+#pragma unroll
+      for (int k = 0; k < B_CPT; ++k) {
+        const int j = lt + k * TEAM;
+        if (j < n) out[j] = xbn[k];
+      }
+    } else {
+      T* ws = reinterpret_cast<T*>(wsp);
+#pragma unroll
+      for (int k = 0; k < B_CPT; ++k) ws[team * TEAM * B_CPT + lt + k * TEAM] = xbn[k];
+      __syncthreads();
+      for (int j = tid; j < n; j += BT) {
+        T s = ws[j];
+        for (int t2 = 1; t2 < NT; ++t2) s += ws[t2 * TEAM * B_CPT + j];
+        out[j] = s;
+      }
+    }
+    __syncthreads();
+    if (lt == 0) red[team] = fn;
+    __syncthreads();
+    double tot = 0.0;
+    for (int t2 = 0; t2 < NT; ++t2) tot += red[t2];
+    __syncthreads();
+    return tot;
+  }
+}
+
+// Elements [w.start, w.start + w.count) of a tet instance; returns the tile's f.
+template <typename T, bool PAIR>
+__device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, const LogConsts& K,
+                           double* red, bool& bad) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int4* conn = static_cast<const int4*>(I.d0);
+  const T* G = static_cast<const T*>(I.d1);
+  const T* u = static_cast<const T*>(I.x);
+  T* gu = static_cast<T*>(I.gx);
+  Acc fp = acc_zero();
+  T fn = T(0);
+  const int64_t e1 = w.start + w.count;
+  int cnt = 0;
+  for (int64_t e = w.start + tid; e < e1; e += BT, ++cnt) {
+    const int4 c = __ldcs(conn + e);
+    if constexpr (PAIR) {
+      elem_pair<TS_GRAD>(c, reinterpret_cast<const double*>(G) + e * 12,
+                         reinterpret_cast<const double*>(u), Pair{2.0f, 0.0f}, tab, K, fp,
+                         reinterpret_cast<double*>(gu), nullptr, bad);
+      if ((cnt & 31) == 31) acc_renorm(fp);
+    } else {
+      elem_native<T, TS_GRAD>(c, G + e * 12, u, T(1), fn, gu, nullptr);
+    }
+  }
+  __syncthreads();
+  if constexpr (PAIR) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fp = acc_add(fp, shfl_xor_acc2(fp, o));
+    Acc* ra = reinterpret_cast<Acc*>(red);
+    if (lane == 0) ra[warp] = fp;
+    __syncthreads();
+    Acc tot = ra[0];
+    for (int q = 1; q < BW; ++q) tot = acc_add(tot, ra[q]);
+    __syncthreads();
+    return acc_to_double(tot);
+  } else {
+    const double t = block_sum((double)fn, red);
+    __syncthreads();
+    return t;
+  }
+}
+
+// Last tile of an instance: sum the tile partials in tile order.
+template <typename T, bool PAIR>
+__device__ void finalize(const BInst& I, double* red) {
+  const int tid = threadIdx.x;
+  if (I.kind == BK_DENSE) {
+    const int n = I.n;
+    for (int j = tid; j < n; j += BT) {
+      if constexpr (PAIR) {
+        const Acc* P = static_cast<const Acc*>(I.partials);
+        Acc s = acc_zero();
+        for (int t = 0; t < I.ntiles; ++t) {
+          const float2 v = __ldcg(reinterpret_cast<const float2*>(P + (int64_t)t * n + j));
+          s = acc_add(s, Acc{v.x, v.y});
+          if ((t & 31) == 31) acc_renorm(s);
+        }
+        static_cast<double*>(I.gx)[j] = pair_to_double_fast(acc_pair(s));
+      } else {
+        const T* P = static_cast<const T*>(I.partials);
+        T s = T(0);
+        for (int t = 0; t < I.ntiles; ++t) s += __ldcg(P + (int64_t)t * n + j);
+        static_cast<T*>(I.gx)[j] = s;
+      }
+    }
+  }
+  if (tid == 0 && I.f) {
+    double fs = 0.0;
+    for (int t = 0; t < I.ntiles; ++t) fs += __ldcg(I.fpart + t);
+    *static_cast<T*>(I.f) = (T)fs;
+  }
+}
+
+template <typename T, bool PAIR>
+__global__ void __launch_bounds__(BT) batched_kernel(BArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float4* tab = reinterpret_cast<float4*>(smem);
+  unsigned char* wsp = smem + (PAIR ? kLogTableSize * sizeof(float4) : 0);
+  double* red = reinterpret_cast<double*>(wsp + (size_t)BT * B_CPT * 8);
+  __shared__ int s_item, s_last;
+  const int tid = threadIdx.x;
+  if constexpr (PAIR) {
+    for (int i = tid; i < kLogTableSize; i += BT) tab[i] = a.logtab[i];
+  }
+  __syncthreads();
+  bool bad = false;
+  for (;;) {
+    if (tid == 0) s_item = (int)atomicAdd(&a.head[0], 1u);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= a.nitems) break;
+    const BItem w = a.items[it];
+    const BInst I = a.insts[w.inst];
+    double ft;
+    if (I.kind == BK_DENSE) {
+      ft = I.team == 32 ? dense_tile<T, PAIR, 32>(I, w, wsp, red, bad)
+                        : dense_tile<T, PAIR, BT>(I, w, wsp, red, bad);
+    } else {
+      ft = tet_tile<T, PAIR>(I, w, tab, a.K, red, bad);
+    }
+    if (tid == 0) I.fpart[w.tile] = ft;
+    __threadfence();
+    __syncthreads();
+    if (tid == 0) s_last = atomicAdd(I.done, 1u) == (unsigned)I.ntiles - 1u;
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      finalize<T, PAIR>(I, red);
+      if (tid == 0) *I.done = 0u;
+    }
+  }
+  if (bad) set_error(a.err, ERRBIT_RANGE);
+  if (tid == 0) {  // the last CTA to leave resets the queue for the next replay
+    __threadfence();
+    if (atomicAdd(&a.head[1], 1u) == gridDim.x - 1) {
+      a.head[0] = 0u;
+      a.head[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+template <typename T>
+__global__ void batched_zero_kernel(const BInst* __restrict__ insts, const int* __restrict__ ids,
+                                    int count) {
+  for (int k = blockIdx.x; k < count; k += gridDim.x) {
+    const BInst I = insts[ids[k]];
+    T* g = static_cast<T*>(I.gx);
+    for (int j = threadIdx.x; j < I.n; j += blockDim.x) g[j] = T(0);
+  }
+}
+
+}  // namespace kg
+
+// ------------------------------------------------------------------ host --
+using namespace kg;
+
+namespace {
+
+size_t batched_smem(bool pair) {
+  return (pair ? kLogTableSize * sizeof(float4) : 0) + (size_t)BT * B_CPT * 8 + 64 * sizeof(double);
+}
+
+int bucket_of(int64_t v) {
+  int b = 0;
+  while ((int64_t(1) << (b + 1)) <= v) ++b;
+  return b;
+}
+
+// ---- tuning cache: one JSON object of "key": value lines ----
+std::mutex g_tune_mu;
+
+std::string cache_path() {
+  if (const char* p = std::getenv("KG_TUNE_CACHE")) return p;
+  const char* home = std::getenv("HOME");
+  return std::string(home ? home : ".") + "/.cache/kg_tune.json";
+}
+
+std::map<std::string, int> cache_read() {
+  std::map<std::string, int> m;
+  std::ifstream in(cache_path());
+  std::string line;
+  while (std::getline(in, line)) {
+    const size_t q1 = line.find('"'), q2 = line.find('"', q1 + 1), c = line.find(':', q2 + 1);
+    if (q1 == std::string::npos || q2 == std::string::npos || c == std::string::npos) continue;
+    m[line.substr(q1 + 1, q2 - q1 - 1)] = std::atoi(line.c_str() + c + 1);
+  }
+  return m;
+}
+
+void cache_write(const std::map<std::string, int>& m) {
+  const std::string path = cache_path();
+  const size_t slash = path.rfind('/');
+  if (slash != std::string::npos) {  // create the parent directories
+    const std::string dir = path.substr(0, slash);
+    for (size_t i = 1; i <= dir.size(); ++i)
+      if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+  }
+  const std::string tmp = path + ".tmp";
+  std::ofstream out(tmp);
+  if (!out) return;
+  out << "{\n";
+  size_t i = 0;
+  for (const auto& kv : m) out << "  \"" << kv.first << "\": " << kv.second << (++i < m.size() ? ",\n" : "\n");
+  out << "}\n";
+  out.close();
+  std::rename(tmp.c_str(), path.c_str());
+}
+
+}  // namespace
+
+namespace {
+
+// ---- plans: instances cut into tiles ----
+struct Plan {
+  std::vector<BInst> insts;
+  std::vector<BItem> items;
+  std::vector<int> tet_ids;
+  std::vector<size_t> part_off;  // byte offset of each dense instance's partials
+  std::vector<size_t> fpart_off; // index of each instance's first f partial
+  size_t part_bytes = 0, fparts = 0;
+};
+
+struct Tuning {
+  std::map<int, int> dense_rows;   // bucket -> rows per item
+  std::map<int, int> tet_elems;    // bucket -> elements per item
+};
+
+int default_rows(int n) { return n <= 256 ? 64 : (n <= 1024 ? 16 : 8); }
+int default_elems(int64_t) { return 4096; }
+
+Plan make_plan(const std::vector<kg_problem*>& probs, const std::vector<int>& ids, const Tuning& tu,
+               bool pair, size_t es) {
+  Plan P;
+  struct Cost {
+    double c;
+    BItem it;
+  };
+  std::vector<Cost> all;
+  for (int idx = 0; idx < (int)ids.size(); ++idx) {
+    const kg_problem* p = probs[ids[idx]];
+    BInst I{};
+    I.kind = p->kind == KG_QUADFORM ? BK_DENSE : BK_TET;
+    I.n = (int)p->n;
+    I.m = p->m;
+    I.d0 = p->data0;
+    I.d1 = p->data1;
+    int64_t per;
+    if (I.kind == BK_DENSE) {
+      auto f = tu.dense_rows.find(bucket_of(p->n));
+      per = f != tu.dense_rows.end() ? f->second : default_rows((int)p->n);
+      I.team = p->n <= 256 ? 32 : BT;
+    } else {
+      auto f = tu.tet_elems.find(bucket_of(p->m));
+      per = f != tu.tet_elems.end() ? f->second : default_elems(p->m);
+      I.team = 0;
+      P.tet_ids.push_back(idx);
+    }
+    I.ntiles = (int)((I.m + per - 1) / per);
+    P.fpart_off.push_back(P.fparts);
+    P.fparts += I.ntiles;
+    P.part_off.push_back(P.part_bytes);
+    if (I.kind == BK_DENSE) {
+      const size_t b = (size_t)I.ntiles * I.n * (pair ? sizeof(Acc) : es);
+      P.part_bytes += (b + 255) & ~size_t(255);
+    }
+    for (int t = 0; t < I.ntiles; ++t) {
+      BItem it{idx, t, (int64_t)t * per, (int)std::min<int64_t>(per, I.m - (int64_t)t * per)};
+      const double bytes = I.kind == BK_DENSE ? (double)it.count * I.n * es
+                                              : (double)it.count * (16.0 + 12.0 * es);
+      all.push_back({bytes, it});
+    }
+    P.insts.push_back(I);
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Cost& a, const Cost& b) { return a.c > b.c; });
+  for (const auto& c : all) P.items.push_back(c.it);
+  return P;
+}
+
+// Device copy of a plan with its workspaces; x/f/gx filled per call.
+struct DevPlan {
+  BInst* insts = nullptr;
+  BItem* items = nullptr;
+  int* tet_ids = nullptr;
+  unsigned* head = nullptr;
+  unsigned* done = nullptr;
+  unsigned char* parts = nullptr;
+  double* fpart = nullptr;
+  int nitems = 0, ntet = 0, ninst = 0;
+  std::vector<void*> allocs;
+  void release() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+  }
+};
+
+kg_status devplan_alloc(DevPlan& D, Plan& P, cudaStream_t s) {
+  auto al = [&](void** ptr, size_t bytes, const char* what) -> kg_status {
+    cudaError_t e = dev_alloc(ptr, bytes);
+    if (e != cudaSuccess) return fail(KG_ERR_OOM, std::string("batch workspace: ") + what);
+    D.allocs.push_back(*ptr);
+    return KG_OK;
+  };
+  kg_status rc;
+  D.ninst = (int)P.insts.size();
+  D.nitems = (int)P.items.size();
+  D.ntet = (int)P.tet_ids.size();
+  if ((rc = al((void**)&D.insts, sizeof(BInst) * P.insts.size(), "descriptors")) != KG_OK) return rc;
+  if ((rc = al((void**)&D.items, sizeof(BItem) * P.items.size(), "work table")) != KG_OK) return rc;
+  if ((rc = al((void**)&D.tet_ids, sizeof(int) * std::max<size_t>(1, P.tet_ids.size()), "tet ids")) != KG_OK) return rc;
+  if ((rc = al((void**)&D.head, 16, "queue head")) != KG_OK) return rc;
+  if ((rc = al((void**)&D.done, sizeof(unsigned) * P.insts.size(), "arrival counters")) != KG_OK) return rc;
+  if ((rc = al((void**)&D.parts, std::max<size_t>(256, P.part_bytes), "partials")) != KG_OK) return rc;
+  if ((rc = al((void**)&D.fpart, sizeof(double) * std::max<size_t>(1, P.fparts), "f partials")) != KG_OK) return rc;
+  for (int i = 0; i < D.ninst; ++i) {
+    P.insts[i].partials = D.parts + P.part_off[i];
+    P.insts[i].fpart = D.fpart + P.fpart_off[i];
+    P.insts[i].done = D.done + i;
+  }
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(D.head, 0, 16, s)) != cudaSuccess) return cuda_fail(e, "batch set-up");
+  if ((e = cudaMemsetAsync(D.done, 0, sizeof(unsigned) * P.insts.size(), s)) != cudaSuccess)
+    return cuda_fail(e, "batch set-up");
+  if ((e = cudaMemcpyAsync(D.items, P.items.data(), sizeof(BItem) * P.items.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "batch set-up");
+  if (!P.tet_ids.empty() &&
+      (e = cudaMemcpyAsync(D.tet_ids, P.tet_ids.data(), sizeof(int) * P.tet_ids.size(),
+                           cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return cuda_fail(e, "batch set-up");
+  return KG_OK;
+}
+
+int batched_grid(bool pair) {
+  int per = 0, dev = 0;
+  cudaGetDevice(&dev);
+  const size_t smem = batched_smem(pair);
+  cudaError_t e;
+  if (pair)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, true>, BT, smem);
+  else
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, false>, BT, smem);
+  if (e != cudaSuccess || per < 1) per = 2;
+  return num_sms() * std::min(per, 4);
+}
+
+// Launches the zero kernel (tet gradients) and the persistent kernel on s.
+kg_status launch_plan(const DevPlan& D, int dtype, bool pair, unsigned* err, cudaStream_t s,
+                      int grid) {
+  cudaError_t e = cudaSuccess;
+  if (D.ntet > 0) {
+    const int zg = std::min(D.ntet, num_sms() * 4);
+    if (dtype == KG_F64) batched_zero_kernel<double><<<zg, 256, 0, s>>>(D.insts, D.tet_ids, D.ntet);
+    else batched_zero_kernel<float><<<zg, 256, 0, s>>>(D.insts, D.tet_ids, D.ntet);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batched zero kernel");
+  }
+  BArgs a{};
+  a.insts = D.insts;
+  a.items = D.items;
+  a.nitems = D.nitems;
+  a.head = D.head;
+  a.err = err;
+  a.K = log_consts();
+  if (pair) {
+    kg_status rc = logtab_for_device(&a.logtab);
+    if (rc != KG_OK) return rc;
+  }
+  const size_t smem = batched_smem(pair);
+  if (dtype == KG_F64) {
+    if (pair) batched_kernel<double, true><<<grid, BT, smem, s>>>(a);
+    else batched_kernel<double, false><<<grid, BT, smem, s>>>(a);
+  } else {
+    batched_kernel<float, false><<<grid, BT, smem, s>>>(a);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batched kernel");
+  return KG_OK;
+}
+
+}  // namespace
+
+struct kg_batch {
+  std::vector<kg_problem*> probs;
+  int dtype = KG_F64;
+  bool pair = false;
+  size_t es = 8;
+  Plan plan;
+  DevPlan dev;
+  unsigned* err = nullptr;
+  int grid = 0;
+  Tuning tune;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> last_x, last_f, last_gx;
+  bool ptrs_valid = false;
+  cudaStream_t last_stream = nullptr;
+  std::string gpu;
+};
+
+namespace {
+
+std::string gpu_name() {
+  int dev = 0;
+  cudaDeviceProp pr{};
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&pr, dev) != cudaSuccess)
+    return "unknown";
+  std::string s = pr.name;
+  for (char& c : s)
+    if (c == '"' || c == '|') c = '_';
+  return s;
+}
+
+// Times the persistent kernel on the instances `ids` with tuning `tu`.
+kg_status time_plan(kg_batch* b, const std::vector<int>& ids, const Tuning& tu, cudaStream_t s,
+                    void* xbuf, void* gbuf, float* ms) {
+  Plan P = make_plan(b->probs, ids, tu, b->pair, b->es);
+  DevPlan D;
+  kg_status rc = devplan_alloc(D, P, s);
+  if (rc == KG_OK) {
+    size_t off = 0;
+    for (auto& I : P.insts) {
+      I.x = static_cast<unsigned char*>(xbuf) + off;
+      I.gx = static_cast<unsigned char*>(gbuf) + off;
+      I.f = nullptr;
+      off += ((size_t)I.n * b->es + 255) & ~size_t(255);
+    }
+    cudaError_t e = cudaMemcpyAsync(D.insts, P.insts.data(), sizeof(BInst) * P.insts.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "autotune");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == KG_OK && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+      rc = fail(KG_ERR_CUDA, "autotune events");
+    float best = 1e30f;
+    for (int r = 0; rc == KG_OK && r < 4; ++r) {
+      cudaEventRecord(e0, s);
+      rc = launch_plan(D, b->dtype, b->pair, b->err, s, b->grid);
+      cudaEventRecord(e1, s);
+      if (rc == KG_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune");
+      float t = 0.f;
+      if (rc == KG_OK && r > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) best = std::min(best, t);
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    *ms = best;
+  }
+  cudaStreamSynchronize(s);
+  D.release();
+  return rc;
+}
+
+// Chooses rows (dense) / elements (tet) per item for every size bucket of the
+// batch: each candidate runs on up to 24 instances of the bucket; the fastest
+// wins.  Choices are cached by GPU name, kind, dtype, arithmetic and bucket.
+kg_status autotune(kg_batch* b, cudaStream_t s) {
+  std::map<std::pair<int, int>, std::vector<int>> groups;  // (kind, bucket) -> instance ids
+  for (int i = 0; i < (int)b->probs.size(); ++i) {
+    const kg_problem* p = b->probs[i];
+    const int kind = p->kind == KG_QUADFORM ? BK_DENSE : BK_TET;
+    groups[{kind, bucket_of(kind == BK_DENSE ? p->n : p->m)}].push_back(i);
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  std::map<std::string, int> cache = cache_read();
+  bool dirty = false;
+  const std::string prefix = b->gpu + "|" + (b->dtype == KG_F64 ? "f64" : "f32") + "|" +
+                             (b->pair ? "pair" : "native") + "|";
+  // scratch x / gx for the timing runs (zeros are valid inputs for both kinds)
+  size_t need = 0;
+  for (auto& g : groups) {
+    size_t sz = 0;
+    for (size_t k = 0; k < g.second.size() && k < 24; ++k)
+      sz += ((size_t)b->probs[g.second[k]]->n * b->es + 255) & ~size_t(255);
+    need = std::max(need, sz);
+  }
+  void *xbuf = nullptr, *gbuf = nullptr;
+  if (dev_alloc(&xbuf, need) != cudaSuccess || dev_alloc(&gbuf, need) != cudaSuccess) {
+    cudaFree(xbuf);
+    return fail(KG_ERR_OOM, "autotune scratch");
+  }
+  cudaMemsetAsync(xbuf, 0, need, s);
+  kg_status rc = KG_OK;
+  for (auto& g : groups) {
+    const int kind = g.first.first, bucket = g.first.second;
+    const std::string key = prefix + (kind == BK_DENSE ? "dense|" : "tet|") + std::to_string(bucket);
+    auto hit = cache.find(key);
+    if (hit != cache.end()) {
+      (kind == BK_DENSE ? b->tune.dense_rows : b->tune.tet_elems)[bucket] = hit->second;
+      continue;
+    }
+    std::vector<int> ids(g.second.begin(), g.second.begin() + std::min<size_t>(24, g.second.size()));
+    std::vector<int> cands = kind == BK_DENSE ? std::vector<int>{4, 8, 16, 32, 64, 128}
+                                              : std::vector<int>{1024, 2048, 4096, 8192, 16384};
+    int best = cands[0];
+    float best_ms = 1e30f;
+    for (int c : cands) {
+      Tuning tu;
+      (kind == BK_DENSE ? tu.dense_rows : tu.tet_elems)[bucket] = c;
+      float ms = 0.f;
+      if ((rc = time_plan(b, ids, tu, s, xbuf, gbuf, &ms)) != KG_OK) break;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = c;
+      }
+    }
+    if (rc != KG_OK) break;
+    (kind == BK_DENSE ? b->tune.dense_rows : b->tune.tet_elems)[bucket] = best;
+    cache[key] = best;
+    dirty = true;
+  }
+  cudaFree(xbuf);
+  cudaFree(gbuf);
+  if (rc == KG_OK && dirty) cache_write(cache);
+  return rc;
+}
+
+void batch_free(kg_batch* b) {
+  if (!b) return;
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->dev.release();
+  if (b->err) cudaFree(b->err);
+  delete b;
+}
+
+}  // namespace
+
+extern "C" {
+
+kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count,
+                          const kg_options* opt, kg_stream stream) {
+  if (!out) return fail(KG_ERR_INVALID_ARG, "kg_batch_create: out is NULL");
+  *out = nullptr;
+  if (!probs || count < 1) return fail(KG_ERR_INVALID_ARG, "kg_batch_create: no problems");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  kg_batch* b = new (std::nothrow) kg_batch();
+  if (!b) return fail(KG_ERR_OOM, "kg_batch_create: host allocation");
+  b->probs.assign(probs, probs + count);
+  b->dtype = b->probs[0] ? b->probs[0]->dtype : KG_F64;
+  b->es = b->dtype == KG_F64 ? 8 : 4;
+  kg_status rc = KG_OK;
+  for (kg_problem* p : b->probs) {
+    if (!p) rc = fail(KG_ERR_INVALID_ARG, "kg_batch_create: NULL problem");
+    else if (p->dtype != b->dtype) rc = fail(KG_ERR_INVALID_ARG, "kg_batch_create: mixed dtypes");
+    else if (p->kind == KG_QUADFORM && p->n > B_MAXN)
+      rc = fail(KG_ERR_UNSUPPORTED, "kg_batch_create: dense instances need n <= 2048");
+    else if (p->kind != KG_QUADFORM && p->kind != KG_TETENERGY)
+      rc = fail(KG_ERR_UNSUPPORTED, "kg_batch_create: QUADFORM and TETENERGY only");
+    if (rc != KG_OK) break;
+  }
+  if (rc == KG_OK && dev_alloc((void**)&b->err, 16) != cudaSuccess)
+    rc = fail(KG_ERR_OOM, "kg_batch_create: error word");
+  if (rc == KG_OK) cudaMemsetAsync(b->err, 0, 16, s);
+  // FP64 arithmetic of the batch: pairs when every instance's data is in range
+  if (rc == KG_OK && b->dtype == KG_F64) {
+    const int want = opt ? opt->arith : KG_ARITH_AUTO;
+    bool pair = want != KG_ARITH_NATIVE;
+    for (kg_problem* p : b->probs) {
+      if (!pair) break;
+      if (p->arith == KG_ARITH_PAIR) continue;
+      if (p->kind == KG_TETENERGY) {
+        pair = false;
+        break;
+      }
+      bool ok = false;
+      if ((rc = pair_range_ok(p, static_cast<const double*>(p->data0), p->m * p->n, s, &ok)) != KG_OK)
+        break;
+      pair = ok;
+    }
+    if (rc == KG_OK && want == KG_ARITH_PAIR && !pair)
+      rc = fail(KG_ERR_UNSUPPORTED, "kg_batch_create: some data is outside the pair range");
+    b->pair = pair;
+  }
+  if (rc == KG_OK) {
+    b->gpu = gpu_name();
+    b->grid = batched_grid(b->pair);
+    if (b->pair) {
+      const float4* t = nullptr;
+      rc = logtab_for_device(&t);
+    }
+    const char* no_tune = std::getenv("KG_NO_AUTOTUNE");
+    if (rc == KG_OK && !(no_tune && no_tune[0] == '1')) rc = autotune(b, s);
+  }
+  if (rc == KG_OK) {
+    std::vector<int> ids(count);
+    for (int i = 0; i < count; ++i) ids[i] = i;
+    b->plan = make_plan(b->probs, ids, b->tune, b->pair, b->es);
+    rc = devplan_alloc(b->dev, b->plan, s);
+  }
+  if (rc == KG_OK) {
+    cudaError_t e = cudaFuncSetAttribute(batched_kernel<double, true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batched_smem(true));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "kg_batch_create");
+  }
+  if (rc != KG_OK) {
+    batch_free(b);
+    return rc;
+  }
+  b->last_stream = s;
+  *out = b;
+  return KG_OK;
+}
+
+static kg_status batch_update_ptrs(kg_batch* b, const void* const* x, void* const* f,
+                                   void* const* gx, cudaStream_t s) {
+  const int n = (int)b->probs.size();
+  for (int i = 0; i < n; ++i)
+    if (!x[i] || !gx[i]) return fail(KG_ERR_INVALID_ARG, "kg_grad_batched: NULL x or gx entry");
+  bool same = b->ptrs_valid;
+  for (int i = 0; same && i < n; ++i)
+    same = b->last_x[i] == x[i] && b->last_f[i] == f[i] && b->last_gx[i] == gx[i];
+  if (same) return KG_OK;
+  b->last_x.assign(x, x + n);
+  b->last_f.assign(f, f + n);
+  b->last_gx.assign(gx, gx + n);
+  for (int i = 0; i < n; ++i) {
+    b->plan.insts[i].x = x[i];
+    b->plan.insts[i].f = f[i];
+    b->plan.insts[i].gx = gx[i];
+  }
+  cudaError_t e = cudaMemcpyAsync(b->dev.insts, b->plan.insts.data(), sizeof(BInst) * n,
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e, "kg_grad_batched: descriptor update");
+  b->ptrs_valid = true;
+  return KG_OK;
+}
+
+kg_status kg_grad_batched(kg_batch* b, const void* const* x, void* const* f, void* const* gx,
+                          kg_stream stream) {
+  reset_launch_count();
+  if (!b || !x || !f || !gx) return fail(KG_ERR_INVALID_ARG, "kg_grad_batched: NULL argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  b->last_stream = s;
+  kg_status rc = batch_update_ptrs(b, x, f, gx, s);
+  if (rc != KG_OK) return rc;
+  cudaError_t e;
+  if (!b->exec) {  // capture the launch sequence once, replay it afterwards
+    cudaStream_t cs = nullptr;
+    if ((e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking)) != cudaSuccess)
+      return cuda_fail(e, "kg_grad_batched: capture stream");
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rc = launch_plan(b->dev, b->dtype, b->pair, b->err, cs, b->grid);
+      cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
+      if (rc == KG_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "kg_grad_batched: end capture");
+    } else {
+      rc = cuda_fail(e, "kg_grad_batched: begin capture");
+    }
+    cudaStreamDestroy(cs);
+    if (rc != KG_OK) return rc;
+    if ((e = cudaGraphInstantiate(&b->exec, b->graph, 0)) != cudaSuccess) {
+      b->exec = nullptr;
+      return cuda_fail(e, "kg_grad_batched: instantiate");
+    }
+  }
+  if ((e = cudaGraphLaunch(b->exec, s)) != cudaSuccess) return cuda_fail(e, "kg_grad_batched: launch");
+  count_launch(b->dev.ntet > 0 ? 2 : 1);
+  return KG_OK;
+}
+
+kg_status kg_grad_batched_loop(kg_batch* b, const void* const* x, void* const* f, void* const* gx,
+                               kg_stream stream) {
+  if (!b || !x || !f || !gx) return fail(KG_ERR_INVALID_ARG, "kg_grad_batched_loop: NULL argument");
+  int launches = 0;
+  for (size_t i = 0; i < b->probs.size(); ++i) {
+    kg_status rc = kg_grad(b->probs[i], x[i], f[i], gx[i], nullptr, nullptr, 0, stream);
+    if (rc != KG_OK) return rc;
+    launches += kg_last_launch_count();
+  }
+  reset_launch_count();
+  count_launch(launches);
+  return KG_OK;
+}
+
+kg_status kg_batch_sync(kg_batch* b) {
+  if (!b) return fail(KG_ERR_INVALID_ARG, "kg_batch_sync: NULL batch");
+  cudaError_t e = cudaStreamSynchronize(b->last_stream);
+  if (e != cudaSuccess) return cuda_fail(e, "kg_batch_sync");
+  unsigned h = 0;
+  if ((e = cudaMemcpy(&h, b->err, sizeof(h), cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(e, "kg_batch_sync");
+  if (h) cudaMemset(b->err, 0, sizeof(unsigned));
+  if (h & ERRBIT_RANGE)
+    return fail(KG_ERR_RANGE, "device: an input is outside the float-pair range");
+  if (h & ERRBIT_TIMEOUT) return fail(KG_ERR_TIMEOUT, "device: a bounded wait gave up");
+  return KG_OK;
+}
+
+void kg_batch_destroy(kg_batch* b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->last_stream);
+  batch_free(b);
+}
+
+}  // extern "C"

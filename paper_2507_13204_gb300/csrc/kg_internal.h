@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/kg.h"
+#include "kg_pair.cuh"
 
 namespace kg {
 
@@ -97,6 +98,10 @@ int qf_pair_grid(const kg_problem* p, int* band);
 kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
                        int accumulate, cudaStream_t s);
+
+// log1p table (256 float4 per device, uploaded once) and constants (tet_pair.cu)
+kg_status logtab_for_device(const float4** out);
+LogConsts log_consts();
 
 // staged tet kernels (tet_pair.cu); mode 0 eval, 1 grad (atomic scatter), 2 tape
 int tet_staged_grid(const kg_problem* p);

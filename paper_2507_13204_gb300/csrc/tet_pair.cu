@@ -24,6 +24,7 @@
 #include "kg_device.cuh"
 #include "kg_internal.h"
 #include "kg_pair.cuh"
+#include "kg_tet_elem.cuh"
 
 namespace kg {
 
@@ -31,7 +32,6 @@ constexpr int TS_THREADS = 256;  // threads per CTA == elements per tile
 constexpr int TS_WARPS = TS_THREADS / 32;
 constexpr int TS_STAGES = 2;
 
-enum { TS_EVAL = 0, TS_GRAD = 1, TS_TAPE = 2 };
 
 template <typename T>
 struct TsArgs {
@@ -51,114 +51,6 @@ struct TsArgs {
   const float4* logtab;  // PAIR: 256 entries
   LogConsts K;
 };
-
-__device__ __forceinline__ Acc shfl_xor_acc2(Acc a, int o) {
-  Acc b;
-  b.s = __shfl_xor_sync(0xffffffffu, a.s, o);
-  b.l = __shfl_xor_sync(0xffffffffu, a.l, o);
-  return b;
-}
-
-template <typename T>
-__device__ __forceinline__ T log1p_nat(T v) {
-  if constexpr (sizeof(T) == 8) return log1p(v);
-  else return log1pf(v);
-}
-
-// One element in native arithmetic (T = float or double).
-template <typename T, int MODE>
-__device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ Gs,
-                                            const T* __restrict__ u, T fb, T& facc, T* gu,
-                                            T* tape_e) {
-  T G[12];
-#pragma unroll
-  for (int i = 0; i < 12; ++i) G[i] = Gs[i];
-  const T u0 = __ldg(u + c.x), u1 = __ldg(u + c.y), u2 = __ldg(u + c.z), u3 = __ldg(u + c.w);
-  const T g0 = G[0] * u0 + G[1] * u1 + G[2] * u2 + G[3] * u3;
-  const T g1 = G[4] * u0 + G[5] * u1 + G[6] * u2 + G[7] * u3;
-  const T g2 = G[8] * u0 + G[9] * u1 + G[10] * u2 + G[11] * u3;
-  const T s = g0 * g0 + g1 * g1 + g2 * g2;
-  facc += log1p_nat(s);
-  if constexpr (MODE != TS_EVAL) {
-    const T w = T(2) * fb / (T(1) + s);
-    const T w0 = w * g0, w1 = w * g1, w2 = w * g2;
-    const T c0 = G[0] * w0 + G[4] * w1 + G[8] * w2;
-    const T c1 = G[1] * w0 + G[5] * w1 + G[9] * w2;
-    const T c2 = G[2] * w0 + G[6] * w1 + G[10] * w2;
-    const T c3 = G[3] * w0 + G[7] * w1 + G[11] * w2;
-    if constexpr (MODE == TS_GRAD) {
-      atomicAdd(gu + c.x, c0);
-      atomicAdd(gu + c.y, c1);
-      atomicAdd(gu + c.z, c2);
-      atomicAdd(gu + c.w, c3);
-    } else {
-      tape_e[0] = c0;
-      tape_e[1] = c1;
-      tape_e[2] = c2;
-      tape_e[3] = c3;
-    }
-  }
-}
-
-// One element in float-pair arithmetic (FP64 data).
-template <int MODE>
-__device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict__ Gs,
-                                          const double* __restrict__ u, Pair fb2,
-                                          const float4* __restrict__ tab, const LogConsts& K,
-                                          Acc& facc, double* gu, double* tape_e, bool& bad) {
-  Pair G[12];
-#pragma unroll
-  for (int i = 0; i < 12; i += 2) {
-    const double2 v = *reinterpret_cast<const double2*>(Gs + i);
-    G[i] = split_f64(v.x);
-    G[i + 1] = split_f64(v.y);
-  }
-  const double ud[4] = {__ldg(u + c.x), __ldg(u + c.y), __ldg(u + c.z), __ldg(u + c.w)};
-  Pair U[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    bad |= !pair_in_range(ud[k]);
-    U[k] = split_f64(ud[k]);
-  }
-  Pair g[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    Acc a = acc_zero();
-#pragma unroll
-    for (int k = 0; k < 4; ++k) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, U[k].h, U[k].l);
-    g[r] = acc_pair(a);
-  }
-  Acc sa = acc_zero();
-#pragma unroll
-  for (int r = 0; r < 3; ++r) acc_fma(sa, g[r].h, g[r].l, g[r].h, g[r].l);
-  const Pair s = acc_pair(sa);
-  Pair t;
-  const Pair lf = pair_log1p(s, tab, K, t);
-  facc = acc_add(facc, Acc{lf.h, lf.l});
-  if constexpr (MODE != TS_EVAL) {
-    const Pair w = pair_mul(fb2, pair_recip(t));
-    Pair wg[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) wg[r] = pair_mul(w, g[r]);
-    double cd[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      Acc a = acc_zero();
-#pragma unroll
-      for (int r = 0; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, wg[r].h, wg[r].l);
-      cd[k] = pair_to_double_fast(acc_pair(a));
-    }
-    if constexpr (MODE == TS_GRAD) {
-      atomicAdd(gu + c.x, cd[0]);
-      atomicAdd(gu + c.y, cd[1]);
-      atomicAdd(gu + c.z, cd[2]);
-      atomicAdd(gu + c.w, cd[3]);
-    } else {
-      reinterpret_cast<double2*>(tape_e)[0] = make_double2(cd[0], cd[1]);
-      reinterpret_cast<double2*>(tape_e)[1] = make_double2(cd[2], cd[3]);
-    }
-  }
-}
 
 template <typename T, bool PAIR, int MODE>
 __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
@@ -300,7 +192,7 @@ static void split_ld(long double v, float& h, float& l) {
   l = (float)(v - (long double)h);
 }
 
-static LogConsts log_consts() {
+LogConsts log_consts() {
   LogConsts K;
   split_ld(logl(2.0L), K.ln2_h, K.ln2_l);
   split_ld(1.0L / 3.0L, K.third_h, K.third_l);
@@ -309,7 +201,7 @@ static LogConsts log_consts() {
 
 // The 256-entry table (log c_k, 1/c_k) for c_k = 1 + k/256, computed on the
 // host in extended precision and uploaded once per device (kept until exit).
-static kg_status logtab_for_device(const float4** out) {
+kg_status logtab_for_device(const float4** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");

@@ -1,0 +1,122 @@
+"""GPU parity of the batched persistent launch: every instance of a mixed
+dense + tet batch equals its single-instance oracle result; graph replays after
+the inputs change and after the buffer pointers change."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2507_13204_gb300 import workloads as W
+from tests.helpers import TOL, f32_round, rel_l2, rel_scalar
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api(cuda_ok):
+    from paper_2507_13204_gb300 import build
+    build.build()
+    from paper_2507_13204_gb300 import api as A
+    return A
+
+
+def _make(api, dtype, dense_ns, tet_boxes, seed=0):
+    td = torch.float64 if dtype == "f64" else torch.float32
+    rnd = (lambda a: a) if dtype == "f64" else f32_round
+    probs, host, xs, fs, gxs = [], [], [], [], []
+    for k, n in enumerate(dense_ns):
+        A, x = W.quadform_inputs(n, seed=seed + k)
+        A, x = rnd(A), rnd(x)
+        p = api.QuadForm(torch.tensor(A, dtype=td, device="cuda"))
+        probs.append(p)
+        host.append(("dense", A, x))
+        xs.append(torch.tensor(x, dtype=td, device="cuda"))
+    for k, box in enumerate(tet_boxes):
+        mesh, u = W.batched_tet_instance(k, box)
+        G, u = rnd(mesh.G), rnd(u)
+        p = api.TetEnergy(torch.tensor(mesh.conn, device="cuda"),
+                          torch.tensor(G, dtype=td, device="cuda"), mesh.nv)
+        probs.append(p)
+        host.append(("tet", mesh.conn, G, u))
+        xs.append(torch.tensor(u, dtype=td, device="cuda"))
+    for x in xs:
+        fs.append(torch.empty((), dtype=td, device="cuda"))
+        gxs.append(torch.full_like(x, 3.0))
+    return probs, host, xs, fs, gxs
+
+
+def _oracle(h):
+    if h[0] == "dense":
+        return O.quadform_grad(h[1], h[2])
+    return O.tet_grad(h[1], h[2], h[3])
+
+
+DENSE = [32, 33, 64, 100, 255, 256, 257, 511, 1000, 1024, 1500, 2047, 2048]
+BOXES = [(1, 1, 1), (3, 3, 2), (5, 5, 7), (10, 10, 12)]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_batched_matches_oracle_per_instance(api, dtype, tmp_path, monkeypatch):
+    monkeypatch.setenv("KG_TUNE_CACHE", str(tmp_path / "tune.json"))
+    probs, host, xs, fs, gxs = _make(api, dtype, DENSE, BOXES)
+    batch = api.Batch(probs)
+    batch.grad(xs, fs, gxs)
+    batch.sync()
+    tol = TOL[dtype]
+    for h, f, g in zip(host, fs, gxs):
+        f_ref, g_ref = _oracle(h)
+        assert rel_scalar(f.item(), f_ref) <= tol, h[0]
+        assert rel_l2(g.cpu().numpy(), g_ref) <= tol, h[0]
+    assert (tmp_path / "tune.json").exists()
+    # the per-instance launch loop gives the same results
+    fl = [torch.empty_like(f) for f in fs]
+    gl = [torch.empty_like(g) for g in gxs]
+    batch.grad_loop(xs, fl, gl)
+    torch.cuda.synchronize()
+    for g, h2 in zip(gxs, gl):
+        assert rel_l2(h2.cpu().numpy(), g.cpu().numpy()) <= tol
+
+
+def test_graph_replay_after_inputs_and_pointers_change(api, tmp_path, monkeypatch):
+    monkeypatch.setenv("KG_TUNE_CACHE", str(tmp_path / "tune.json"))
+    probs, host, xs, fs, gxs = _make(api, "f64", [64, 700, 2000], [(4, 4, 4)], seed=5)
+    batch = api.Batch(probs)
+    batch.grad(xs, fs, gxs)
+    first = [g.clone() for g in gxs]
+    batch.grad(xs, fs, gxs)  # replay: dense results are bitwise reproducible
+    torch.cuda.synchronize()
+    for a, b, h in zip(first, gxs, host):
+        if h[0] == "dense":
+            assert torch.equal(a, b)
+    # mutate x in place and replay
+    for x in xs:
+        x.mul_(0.5)
+    batch.grad(xs, fs, gxs)
+    batch.sync()
+    for h, x, f, g in zip(host, xs, fs, gxs):
+        hx = x.cpu().numpy()
+        ref = O.quadform_grad(h[1], hx) if h[0] == "dense" else O.tet_grad(h[1], h[2], hx)
+        assert rel_scalar(f.item(), ref[0]) <= TOL["f64"]
+        assert rel_l2(g.cpu().numpy(), ref[1]) <= TOL["f64"]
+    # new buffers (pointer tables change): the descriptors are refreshed
+    xs2 = [x.clone() * 2 for x in xs]
+    gxs2 = [torch.empty_like(g) for g in gxs]
+    batch.grad(xs2, fs, gxs2)
+    batch.sync()
+    for h, x, g in zip(host, xs2, gxs2):
+        hx = x.cpu().numpy()
+        ref = O.quadform_grad(h[1], hx) if h[0] == "dense" else O.tet_grad(h[1], h[2], hx)
+        assert rel_l2(g.cpu().numpy(), ref[1]) <= TOL["f64"]
+
+
+def test_batch_rejects_bad_inputs(api):
+    from paper_2507_13204_gb300 import _lib as L
+    big = api.QuadForm(torch.zeros((4, 4096), dtype=torch.float64, device="cuda"))
+    with pytest.raises(L.KGError) as ei:
+        api.Batch([big])
+    assert ei.value.status == L.KG_ERR_UNSUPPORTED
+    a = api.QuadForm(torch.zeros((8, 8), dtype=torch.float64, device="cuda"))
+    b = api.QuadForm(torch.zeros((8, 8), dtype=torch.float32, device="cuda"))
+    with pytest.raises(L.KGError) as ei:
+        api.Batch([a, b])
+    assert ei.value.status == L.KG_ERR_INVALID_ARG
