@@ -197,6 +197,10 @@ kg_status kg_batch_create(kg_batch **out, kg_problem *const *probs, int count,
 kg_status kg_grad_batched(kg_batch *b, const void *const *x, void *const *f, void *const *gx,
                           kg_stream s);
 
+/* The batch's resolved FP64 arithmetic (kg_arith), number of work items in
+ * its device table and persistent grid size.  Any pointer may be NULL. */
+kg_status kg_batch_get_config(const kg_batch *b, int *arith, int *items, int *grid);
+
 /* Same work as kg_grad_batched, issued as one kg_grad launch sequence per
  * instance on `s` (the per-instance launch loop the batch is compared with). */
 kg_status kg_grad_batched_loop(kg_batch *b, const void *const *x, void *const *f,

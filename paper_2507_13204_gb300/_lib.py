@@ -27,7 +27,7 @@ KG_ARITH_AUTO, KG_ARITH_NATIVE, KG_ARITH_PAIR = range(3)
 # Every symbol include/kg.h declares (checked by the test suite).
 EXPORTS = ["kg_options_default", "kg_create", "kg_eval", "kg_grad", "kg_eval_tape",
            "kg_grad_from_tape", "kg_grad_host", "kg_batch_create", "kg_grad_batched",
-           "kg_grad_batched_loop", "kg_sync", "kg_batch_sync", "kg_last_error",
+           "kg_grad_batched_loop", "kg_batch_get_config", "kg_sync", "kg_batch_sync", "kg_last_error",
            "kg_get_config", "kg_workspace_bytes", "kg_last_launch_count", "kg_profile_enable", "kg_profile_read",
            "kg_quadform_grad_noalloc", "kg_destroy", "kg_batch_destroy"]
 
@@ -74,6 +74,7 @@ def lib():
                 "kg_batch_create": (st, [ctypes.POINTER(vp), vpp, i, optp, vp]),
                 "kg_grad_batched": (st, [vp, vpp, vpp, vpp, vp]),
                 "kg_grad_batched_loop": (st, [vp, vpp, vpp, vpp, vp]),
+                "kg_batch_get_config": (st, [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]),
                 "kg_sync": (st, [vp]),
                 "kg_batch_sync": (st, [vp]),
                 "kg_last_error": (ctypes.c_char_p, []),
@@ -187,6 +188,14 @@ def kg_grad_batched(b, xs, fs, gxs, stream=None):
 def kg_grad_batched_loop(b, xs, fs, gxs, stream=None):
     check(lib().kg_grad_batched_loop(b, _table(xs), _table(fs), _table(gxs), stream_handle(stream)),
           "kg_grad_batched_loop")
+
+
+def kg_batch_get_config(b):
+    """(arith name, work items, persistent grid) of a batch."""
+    a, n, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    check(lib().kg_batch_get_config(b, ctypes.byref(a), ctypes.byref(n), ctypes.byref(g)),
+          "kg_batch_get_config")
+    return ["auto", "native", "pair"][a.value], n.value, g.value
 
 
 def kg_sync(h):

@@ -155,6 +155,11 @@ class Batch:
         opt = L.options(dtype=_DT[self.problems[0].dtype], arith=ARITHS[arith])
         self.handle = L.kg_batch_create([p.handle for p in self.problems], opt, stream)
 
+    @property
+    def config(self):
+        """(arith, work items, persistent grid)."""
+        return L.kg_batch_get_config(self.handle)
+
     def grad(self, xs, fs, gxs, stream=None):
         L.kg_grad_batched(self.handle, xs, fs, gxs, stream)
 

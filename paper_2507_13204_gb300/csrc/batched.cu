@@ -84,6 +84,17 @@ struct BArgs {
 };
 
 // ------------------------------------------------------------- device ----
+// L2 prefetch of the whole 16-byte units inside [p, p + bytes) (never beyond).
+__device__ __forceinline__ void prefetch_range_l2(const void* p, size_t bytes) {
+  uintptr_t a = (reinterpret_cast<uintptr_t>(p) + 15) & ~uintptr_t(15);
+  const uintptr_t b = (reinterpret_cast<uintptr_t>(p) + bytes) & ~uintptr_t(15);
+  while (a < b) {
+    const uint32_t chunk = (uint32_t)((b - a) < (uintptr_t(1) << 16) ? (b - a) : (uintptr_t(1) << 16));
+    prefetch_l2_bulk(reinterpret_cast<const void*>(a), chunk);
+    a += chunk;
+  }
+}
+
 template <bool PAIR, typename T>
 __device__ __forceinline__ void b_split(T v, float& h, float& l) {
   if constexpr (PAIR) {
@@ -96,6 +107,14 @@ __device__ __forceinline__ void b_split(T v, float& h, float& l) {
   }
 }
 
+// Barrier over the TEAM threads of one row team: the whole CTA for TEAM = BT,
+// otherwise hardware barrier 1 + team (TEAM = 64 or 128).
+template <int TEAM>
+__device__ __forceinline__ void team_barrier(int team) {
+  if constexpr (TEAM == BT) __syncthreads();
+  else named_barrier(1 + team, TEAM);
+}
+
 // Rows [w.start, w.start + w.count) of a dense instance; returns the tile's f.
 template <typename T, bool PAIR, int TEAM>
 __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp, double* red,
@@ -106,6 +125,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
   const T* __restrict__ x = static_cast<const T*>(I.x);
   constexpr int NT = BT / TEAM;
   const int lt = tid % TEAM, team = tid / TEAM;
+  const int cpt = (n + TEAM - 1) / TEAM;  // <= B_CPT, uniform over the item
   float xh[B_CPT], xl[B_CPT];
   T xv[B_CPT];
   Acc xbp[B_CPT];
@@ -113,7 +133,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
 #pragma unroll
   for (int k = 0; k < B_CPT; ++k) {
     const int j = lt + k * TEAM;
-    xv[k] = j < n ? x[j] : T(0);
+    xv[k] = (k < cpt && j < n) ? x[j] : T(0);
     if constexpr (PAIR) {
       bad |= !pair_in_range((double)xv[k]);
       b_split<PAIR>(xv[k], xh[k], xl[k]);
@@ -125,35 +145,52 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
   double fn = 0.0;
   const int64_t r1 = w.start + w.count;
   const int iters = (w.count + NT - 1) / NT;
-  for (int itr = 0; itr < iters; ++itr) {
-    const int64_t r = w.start + (int64_t)itr * NT + team;
-    const bool valid = r < r1;
-    const T* Ar = A + (valid ? r : w.start) * (int64_t)n;
-    float ah[B_CPT], al[B_CPT];
-    T av[B_CPT];
+  // software pipeline: the next row's loads are in flight while this row computes
+  T an[B_CPT];
+  auto load_row = [&](int itr_, T* dst) {
+    const int64_t r = w.start + (int64_t)itr_ * NT + team;
+    const bool v = itr_ < iters && r < r1;
+    const T* Ar = A + (v ? r : w.start) * (int64_t)n;
 #pragma unroll
     for (int k = 0; k < B_CPT; ++k) {
       const int j = lt + k * TEAM;
-      av[k] = (valid && j < n) ? __ldcs(Ar + j) : T(0);
-      if constexpr (PAIR) b_split<PAIR>(av[k], ah[k], al[k]);
+      dst[k] = (k < cpt && v && j < n) ? __ldcs(Ar + j) : T(0);
+    }
+  };
+  load_row(0, an);
+  for (int itr = 0; itr < iters; ++itr) {
+    const int64_t r = w.start + (int64_t)itr * NT + team;
+    const bool valid = r < r1;
+    float ah[B_CPT], al[B_CPT];
+    T av[B_CPT];
+#pragma unroll
+    for (int k = 0; k < B_CPT; ++k) av[k] = an[k];
+    load_row(itr + 1, an);
+#pragma unroll
+    for (int k = 0; k < B_CPT; ++k) {
+      if constexpr (PAIR) {
+        if (k < cpt) b_split<PAIR>(av[k], ah[k], al[k]);
+        else ah[k] = al[k] = 0.f;
+      }
     }
     if constexpr (PAIR) {
       Acc y0 = acc_zero(), y1 = acc_zero();
 #pragma unroll
       for (int k = 0; k < B_CPT; k += 2) {
-        acc_fma(y0, ah[k], al[k], xh[k], xl[k]);
-        acc_fma(y1, ah[k + 1], al[k + 1], xh[k + 1], xl[k + 1]);
+        if (k < cpt) acc_fma(y0, ah[k], al[k], xh[k], xl[k]);
+        if (k + 1 < cpt) acc_fma(y1, ah[k + 1], al[k + 1], xh[k + 1], xl[k + 1]);
       }
       Acc yv = acc_add(y0, y1);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) yv = acc_add(yv, shfl_xor_acc2(yv, o));
-      if constexpr (TEAM > 32) {
-        Acc* ra = reinterpret_cast<Acc*>(red) + (itr & 1) * BW;
-        if (lane == 0) ra[warp] = yv;
-        __syncthreads();
+      for (int o = (TEAM < 32 ? TEAM : 32) / 2; o > 0; o >>= 1) yv = acc_add(yv, shfl_xor_acc2(yv, o));
+      if constexpr (TEAM > 32) {  // warps of the team exchange through shared memory
+        constexpr int TW = TEAM / 32;
+        Acc* ra = reinterpret_cast<Acc*>(red) + (itr & 1) * BW + team * TW;
+        if (lane == 0) ra[warp % TW] = yv;
+        team_barrier<TEAM>(team);
         yv = ra[0];
 #pragma unroll
-        for (int q = 1; q < BW; ++q) yv = acc_add(yv, ra[q]);
+        for (int q = 1; q < TW; ++q) yv = acc_add(yv, ra[q]);
       }
       if (valid) {
         const Pair y = acc_pair(yv);
@@ -161,7 +198,8 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
         fp = acc_add(fp, Acc{y2.h, y2.l});
         const Pair yb{2.0f * y.h, 2.0f * y.l};  // exact
 #pragma unroll
-        for (int k = 0; k < B_CPT; ++k) acc_fma(xbp[k], ah[k], al[k], yb.h, yb.l);
+        for (int k = 0; k < B_CPT; ++k)
+          if (k < cpt) acc_fma(xbp[k], ah[k], al[k], yb.h, yb.l);
         if ((itr & 15) == 15) {
 #pragma unroll
           for (int k = 0; k < B_CPT; ++k) acc_renorm(xbp[k]);
@@ -170,21 +208,25 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
     } else {
       T d = T(0);
 #pragma unroll
-      for (int k = 0; k < B_CPT; ++k) d = fma(av[k], xv[k], d);
-      d = warp_sum(d);
+      for (int k = 0; k < B_CPT; ++k)
+        if (k < cpt) d = fma(av[k], xv[k], d);
+#pragma unroll
+      for (int o = (TEAM < 32 ? TEAM : 32) / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
       if constexpr (TEAM > 32) {
-        T* rt = reinterpret_cast<T*>(red) + (itr & 1) * BW;
-        if (lane == 0) rt[warp] = d;
-        __syncthreads();
+        constexpr int TW = TEAM / 32;
+        T* rt = reinterpret_cast<T*>(red) + (itr & 1) * BW + team * TW;
+        if (lane == 0) rt[warp % TW] = d;
+        team_barrier<TEAM>(team);
         d = rt[0];
 #pragma unroll
-        for (int q = 1; q < BW; ++q) d += rt[q];
+        for (int q = 1; q < TW; ++q) d += rt[q];
       }
       if (valid) {
         fn += (double)d * (double)d;
         const T yb = T(2) * d;
 #pragma unroll
-        for (int k = 0; k < B_CPT; ++k) xbn[k] = fma(yb, av[k], xbn[k]);
+        for (int k = 0; k < B_CPT; ++k)
+          if (k < cpt) xbn[k] = fma(yb, av[k], xbn[k]);
       }
     }
   }
@@ -341,10 +383,26 @@ __global__ void __launch_bounds__(BT) batched_kernel(BArgs a) {
     if (it >= a.nitems) break;
     const BItem w = a.items[it];
     const BInst I = a.insts[w.inst];
+    if (tid == 0) {  // the tile's contiguous data into L2 while the first loads are in flight
+      if (I.kind == BK_DENSE) {
+        prefetch_range_l2(static_cast<const T*>(I.d0) + w.start * (int64_t)I.n,
+                          (size_t)w.count * I.n * sizeof(T));
+      } else {
+        prefetch_range_l2(static_cast<const int4*>(I.d0) + w.start, (size_t)w.count * 16);
+        prefetch_range_l2(static_cast<const T*>(I.d1) + w.start * 12, (size_t)w.count * 12 * sizeof(T));
+      }
+    }
     double ft;
     if (I.kind == BK_DENSE) {
-      ft = I.team == 32 ? dense_tile<T, PAIR, 32>(I, w, wsp, red, bad)
-                        : dense_tile<T, PAIR, BT>(I, w, wsp, red, bad);
+      switch (I.team) {
+        case 4: ft = dense_tile<T, PAIR, 4>(I, w, wsp, red, bad); break;
+        case 8: ft = dense_tile<T, PAIR, 8>(I, w, wsp, red, bad); break;
+        case 16: ft = dense_tile<T, PAIR, 16>(I, w, wsp, red, bad); break;
+        case 32: ft = dense_tile<T, PAIR, 32>(I, w, wsp, red, bad); break;
+        case 64: ft = dense_tile<T, PAIR, 64>(I, w, wsp, red, bad); break;
+        case 128: ft = dense_tile<T, PAIR, 128>(I, w, wsp, red, bad); break;
+        default: ft = dense_tile<T, PAIR, BT>(I, w, wsp, red, bad); break;
+      }
     } else {
       ft = tet_tile<T, PAIR>(I, w, tab, a.K, red, bad);
     }
@@ -456,7 +514,7 @@ struct Tuning {
   std::map<int, int> tet_elems;    // bucket -> elements per item
 };
 
-int default_rows(int n) { return n <= 256 ? 64 : (n <= 1024 ? 16 : 8); }
+int default_rows(int n) { return n <= 64 ? 128 : n <= 256 ? 64 : (n <= 1024 ? 16 : 8); }
 int default_elems(int64_t) { return 4096; }
 
 Plan make_plan(const std::vector<kg_problem*>& probs, const std::vector<int>& ids, const Tuning& tu,
@@ -479,7 +537,9 @@ Plan make_plan(const std::vector<kg_problem*>& probs, const std::vector<int>& id
     if (I.kind == BK_DENSE) {
       auto f = tu.dense_rows.find(bucket_of(p->n));
       per = f != tu.dense_rows.end() ? f->second : default_rows((int)p->n);
-      I.team = p->n <= 256 ? 32 : BT;
+      // row team: about B_CPT columns per thread (4 .. 256 threads)
+      I.team = 4;
+      while (I.team < BT && (int64_t)I.team * B_CPT < p->n) I.team *= 2;
     } else {
       auto f = tu.tet_elems.find(bucket_of(p->m));
       per = f != tu.tet_elems.end() ? f->second : default_elems(p->m);
@@ -882,7 +942,10 @@ kg_status kg_grad_batched(kg_batch* b, const void* const* x, void* const* f, voi
       return cuda_fail(e, "kg_grad_batched: instantiate");
     }
   }
-  if ((e = cudaGraphLaunch(b->exec, s)) != cudaSuccess) return cuda_fail(e, "kg_grad_batched: launch");
+  prof_begin(s, "batched_kernel (graph)");
+  e = cudaGraphLaunch(b->exec, s);
+  prof_end(s);
+  if (e != cudaSuccess) return cuda_fail(e, "kg_grad_batched: launch");
   count_launch(b->dev.ntet > 0 ? 2 : 1);
   return KG_OK;
 }
@@ -898,6 +961,14 @@ kg_status kg_grad_batched_loop(kg_batch* b, const void* const* x, void* const* f
   }
   reset_launch_count();
   count_launch(launches);
+  return KG_OK;
+}
+
+kg_status kg_batch_get_config(const kg_batch* b, int* arith, int* items, int* grid) {
+  if (!b) return fail(KG_ERR_INVALID_ARG, "kg_batch_get_config: NULL batch");
+  if (arith) *arith = b->pair ? KG_ARITH_PAIR : KG_ARITH_NATIVE;
+  if (items) *items = b->dev.nitems;
+  if (grid) *grid = b->grid;
   return KG_OK;
 }
 

@@ -197,3 +197,15 @@ def batched_tet_instance(k: int, box, seed_base: int = 4000):
 def batched_dense_instance(k: int, n: int, seed_base: int = 3000):
     """Instance k of the dense batch on the host: A (n x n, N(0,1/n)) then x."""
     return quadform_inputs(n, seed=seed_base + k)
+
+
+def batched_dense_device(k: int, n: int, device, seed_base: int = 3000):
+    """Instance k of the dense batch drawn on the device (16.5 GB of A for the
+    4096-instance batch would take minutes on the host): torch's seeded CUDA
+    generator (seed_base + k) draws A (n x n, N(0, 1/n)) and then x (U[-1, 1])."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(seed_base + k)
+    A = torch.randn((n, n), generator=g, dtype=torch.float64, device=device) * math.sqrt(1.0 / n)
+    x = torch.rand(n, generator=g, dtype=torch.float64, device=device) * 2.0 - 1.0
+    return A, x
