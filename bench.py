@@ -449,7 +449,94 @@ class BatchedWL(Workload):
         return done / dt, f"{done} instances (first 64 dense + first 8 tet instances, cycled; oracle, 1 thread)"
 
 
+class AutogradWL(Workload):
+    """Gradient descent u <- u - 0.01 grad f(u) through torch.autograd
+    (KGTetEnergy) on the 6e6-tet mesh; step = one forward + backward + update.
+    The main policy is the tape (forward records c_e, backward scatters it);
+    recompute (backward reruns the fused value-and-gradient kernel) is timed
+    beside it as the comparison."""
+    unit = "steps/s"
+    ETA = 0.01
+
+    def __init__(self, a=100, dtype="f64", arith="auto"):
+        self.a, self.dtype, self.arith = a, dtype, arith
+        self.dtype_name = dtype
+        self.es = 8 if dtype == "f64" else 4
+
+    def setup(self, dev):
+        import torch
+        from paper_2507_13204_gb300 import api, autograd, workloads as W
+        mesh, u = W.tet_inputs(self.a)
+        td = torch.float64 if self.dtype == "f64" else torch.float32
+        self.mesh, self.u_host = mesh, u
+        self.ne, self.nv = mesh.ne, mesh.nv
+        conn = torch.tensor(mesh.conn, device=dev)
+        G = torch.tensor(mesh.G, dtype=td, device=dev)
+        self.p_tape = api.TetEnergy(conn, G, mesh.nv, mode="tape", arith=self.arith)
+        self.p_rec = api.TetEnergy(conn, G, mesh.nv, mode="recompute", arith=self.arith)
+        self.ag = autograd
+        self.u = torch.tensor(u, dtype=td, device=dev)
+        self.u_rec = self.u.clone()
+        self.x_pin = torch.tensor(u, dtype=td).pin_memory()
+        self.g_pin = torch.empty(mesh.nv, dtype=td).pin_memory()
+        self.f_pin = torch.empty((), dtype=td).pin_memory()
+        self.p = self.p_tape
+        self.tape_bytes = 4 * self.ne * self.es
+
+    def _step(self, prob, u, policy):
+        import torch
+        ut = u.requires_grad_(True)
+        f = self.ag.KGTetEnergy.apply(ut, prob, policy)
+        (g,) = torch.autograd.grad(f, ut)
+        return (ut.detach() - self.ETA * g).detach()
+
+    def step(self):
+        self.u = self._step(self.p_tape, self.u, "tape")
+
+    def eval_step(self):  # the recompute policy (the comparison)
+        self.u_rec = self._step(self.p_rec, self.u_rec, "recompute")
+
+    def e2e_step(self):
+        self.p_tape.grad_host(self.x_pin, self.g_pin, self.f_pin)
+
+    @property
+    def grad_bytes(self):  # tape: forward streams conn+G and writes the tape; backward reads conn+tape
+        return self.ne * (16 + 12 * self.es) + 4 * self.ne * self.es + self.ne * 16 + \
+            4 * self.ne * self.es + 3 * self.nv * self.es
+
+    def dominant(self):
+        return (self.ne * (16 + 12 * self.es) + 4 * self.ne * self.es + self.nv * self.es, None)
+
+    def h2d_d2h(self):
+        return self.es * self.nv, self.es * (self.nv + 1)
+
+    def config(self):
+        return {"workload": f"torch.autograd.Function KGTetEnergy, gradient descent (eta 0.01) on "
+                            f"the {self.a}^3 x 6 = {self.ne}-tet mesh, {self.dtype.upper()}",
+                "policy": "tape (main) vs recompute (ms_eval, grad_over_eval_ratio)",
+                "tape_bytes": self.tape_bytes,
+                "l2": "inputs larger than L2"}
+
+    def oracle_sample(self, budget_s=10.0):
+        from oracle import oracle as O
+        ne = min(self.ne, 500_000)
+        conn, G = self.mesh.conn[:ne], self.mesh.G[:ne]
+        t0 = time.perf_counter()
+        steps = 0
+        u = self.u_host.copy()
+        while time.perf_counter() - t0 < budget_s and steps < 50:
+            u, _ = O.tet_descent(conn, G, u, self.ETA, 1)
+            steps += 1
+        dt = time.perf_counter() - t0
+        return steps * ne / self.ne / dt, (f"{steps} descent steps on the first {ne} tets, "
+                                           f"scaled to the full mesh (oracle, 1 thread)")
+
+
 def make_workload(name: str, arith: str, size: int = 0, rows: int = 0):
+    if name == "autograd":
+        return AutogradWL(size or 100, "f64", arith=arith)
+    if name == "autograd32":
+        return AutogradWL(size or 100, "f32")
     if name == "batched":
         return BatchedWL(size or 4096, max(1, (size or 4096) // 8), arith=arith)
     if name == "dense":
@@ -583,6 +670,9 @@ def main():
     elif isinstance(wl, BatchedWL):
         value = world * wl.count * 1000.0 / ms_grad
         e2e_value = world * wl.count * 1000.0 / ms_e2e
+    elif isinstance(wl, AutogradWL):
+        value = world * 1000.0 / ms_grad
+        e2e_value = world * 1000.0 / ms_e2e
     else:
         value = world * wl.grad_bytes / 1e9 / (ms_grad * 1e-3)
         e2e_value = world * wl.grad_bytes / 1e9 / (ms_e2e * 1e-3)
@@ -625,6 +715,9 @@ def main():
         "config": {**wl.config(), "strategy": strategy, "mode": mode, "arith": arith},
         "grad_over_eval_ratio": round(ms_grad / ms_eval, 4),
         "ms_eval": round(ms_eval, 5),
+        **({"autograd": {"tape_ms_per_step": round(ms_grad, 4), "recompute_ms_per_step": round(ms_eval, 4),
+                         "tape_bytes": wl.tape_bytes, "tape_vs_recompute_speedup": round(ms_eval / ms_grad, 3)}}
+           if isinstance(wl, AutogradWL) else {}),
         "pct_of_hbm_peak": round(100 * value / world / peaks["hbm_gbs"], 2) if wl.unit == "GB/s" else None,
         "pct_of_8tbs_nominal": round(100 * value / world / 8000.0, 2) if wl.unit == "GB/s" else None,
         "roofline": roof,
