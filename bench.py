@@ -558,6 +558,23 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0):
     raise SystemExit(f"unknown workload {name}")
 
 
+# ------------------------------------------------------------------ ranks
+def sync_max(values, dist=None, device="cpu"):
+    """Max over ranks of each entry of `values` (identity without a process group)."""
+    if dist is None:
+        return [float(v) for v in values]
+    import torch
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units of all ranks per second, timed by the slowest rank (weak scaling: every
+    rank runs its own replica of the workload)."""
+    return world * units_per_rank / (ms_max * 1e-3)
+
+
 # ------------------------------------------------------------------ main
 def main():
     ap = argparse.ArgumentParser()
@@ -641,10 +658,7 @@ def main():
     Ke = max(3, min(K, int(3000.0 / max(t_probe_e, 1e-3))))
     ms_eval = timed(wl.eval_step, Ke)
 
-    if dist:
-        t = torch.tensor([ms_grad, ms_eval], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_grad, ms_eval = float(t[0]), float(t[1])
+    ms_grad, ms_eval = sync_max([ms_grad, ms_eval], dist, dev)
 
     # end-to-end: host buffers through the C ABI, copies inside the timed region
     K2 = max(5, min(K, int(2000.0 / max(ms_grad, 1e-3))))
@@ -656,28 +670,21 @@ def main():
         wl.e2e_step()
     barrier()
     ms_e2e = (time.perf_counter() - t0) * 1e3 / K2
-    if dist:
-        t = torch.tensor([ms_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t[0])
+    (ms_e2e,) = sync_max([ms_e2e], dist, dev)
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
-    if isinstance(wl, LaplaceWL):
-        value = world * 1000.0 / ms_grad
-        e2e_value = world * 1000.0 / ms_e2e
+    if isinstance(wl, (LaplaceWL, AutogradWL)):
+        units = 1.0
     elif isinstance(wl, BatchedWL):
-        value = world * wl.count * 1000.0 / ms_grad
-        e2e_value = world * wl.count * 1000.0 / ms_e2e
-    elif isinstance(wl, AutogradWL):
-        value = world * 1000.0 / ms_grad
-        e2e_value = world * 1000.0 / ms_e2e
+        units = wl.count
     else:
-        value = world * wl.grad_bytes / 1e9 / (ms_grad * 1e-3)
-        e2e_value = world * wl.grad_bytes / 1e9 / (ms_e2e * 1e-3)
+        units = wl.grad_bytes / 1e9
+    value = whole_job_rate(units, world, ms_grad)
+    e2e_value = whole_job_rate(units, world, ms_e2e)
     # dominant kernel roofline
     per_launch_ms = kern_ms / max(kern_n, 1)
     dbytes, dflops = wl.dominant()
