@@ -55,6 +55,12 @@ __device__ __forceinline__ void finish_sum(double partial, double* fpart, unsign
   }
 }
 
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ void set_error(unsigned* err, unsigned bit) {
   if (err) atomicOr(err, bit);
 }

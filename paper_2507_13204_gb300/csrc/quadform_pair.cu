@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
     ya.s = __shfl_sync(0xffffffffu, ya.s, 0);
     ya.l = __shfl_sync(0xffffffffu, ya.l, 0);
     const Pair y = acc_pair(ya);
-    {  // f in pair arithmetic: no FP64 instruction in the row loop
+    if (t == 0) {  // f in pair arithmetic: no FP64 instruction in the row loop
       const Pair y2 = pair_mul(y, y);
       facc = acc_add(facc, Acc{y2.h, y2.l});
     }
@@ -241,8 +241,23 @@ __global__ void __launch_bounds__(512) qf_pair_reduce_kernel(const float4* __res
   const int jp = blockIdx.x * CX + cx;
   Acc s0 = acc_zero(), s1 = acc_zero();
   if (jp < npairs) {
-    for (int c = py; c < nparts; c += PY) {
-      const float4 v = partials[(int64_t)c * npairs + jp];
+    int c = py;
+    for (; c + 3 * PY < nparts; c += 4 * PY) {  // four independent loads in flight
+      const float4 v0 = __ldcs(partials + (int64_t)c * npairs + jp);
+      const float4 v1 = __ldcs(partials + (int64_t)(c + PY) * npairs + jp);
+      const float4 v2 = __ldcs(partials + (int64_t)(c + 2 * PY) * npairs + jp);
+      const float4 v3 = __ldcs(partials + (int64_t)(c + 3 * PY) * npairs + jp);
+      s0 = acc_add(s0, Acc{v0.x, v0.y});
+      s1 = acc_add(s1, Acc{v0.z, v0.w});
+      s0 = acc_add(s0, Acc{v1.x, v1.y});
+      s1 = acc_add(s1, Acc{v1.z, v1.w});
+      s0 = acc_add(s0, Acc{v2.x, v2.y});
+      s1 = acc_add(s1, Acc{v2.z, v2.w});
+      s0 = acc_add(s0, Acc{v3.x, v3.y});
+      s1 = acc_add(s1, Acc{v3.z, v3.w});
+    }
+    for (; c < nparts; c += PY) {
+      const float4 v = __ldcs(partials + (int64_t)c * npairs + jp);
       s0 = acc_add(s0, Acc{v.x, v.y});
       s1 = acc_add(s1, Acc{v.z, v.w});
     }
