@@ -38,6 +38,7 @@ struct QfConfig {
   int cpt = 1;      // columns per team thread (compile-time variant)
   int grid = 1;     // CTAs
   int rows_per_cta = 1;
+  int streamed = 0;  // 1: FP32 TMA-streamed kernel (quadform_f32.cu)
 };
 
 struct kg_problem_impl;
@@ -89,6 +90,13 @@ kg_status qf_grad(kg_problem* p, const void* x, void* f, void* gx, void* gA, con
 kg_status qf_native_fused_on_scratch(const double* A, int64_t m, int64_t n, const double* x,
                                      double* f, double* gx, double* scratch,
                                      size_t scratch_doubles, cudaStream_t s);
+
+// FP32 TMA-streamed dense kernels (quadform_f32.cu)
+bool qf_f32_supported(const kg_problem* p);
+int qf_f32_grid(const kg_problem* p, int* band);
+kg_status qf_f32_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
+kg_status qf_f32_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
+                      int accumulate, cudaStream_t s);
 
 // float-pair dense kernels (quadform_pair.cu)
 bool qf_pair_supported(const kg_problem* p);

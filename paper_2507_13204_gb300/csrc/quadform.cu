@@ -357,6 +357,16 @@ kg_status qf_setup(kg_problem* p, cudaStream_t s) {
     return rc;
   }
   if (p->arith == KG_ARITH_AUTO || p->dtype == KG_F32) p->arith = KG_ARITH_NATIVE;
+  if (qf_f32_supported(p)) {  // FP32: rows streamed through shared memory by TMA
+    p->strategy = KG_STRATEGY_FUSED;
+    QfConfig& c = p->qf;
+    c.streamed = 1;
+    c.grid = qf_f32_grid(p, &c.rows_per_cta);
+    c.team = c.block = 512;
+    kg_status rc = ws_common(p, c.grid, s);
+    if (rc != KG_OK) return rc;
+    return ws_alloc(p, &p->partials, 4 * (size_t)c.grid * p->n, "xbar partials (FP32)");
+  }
   if (p->strategy == KG_STRATEGY_AUTO) p->strategy = var >= 0 ? KG_STRATEGY_FUSED : KG_STRATEGY_TRANSPOSE;
   if (var < 0) {
     if (p->strategy != KG_STRATEGY_TRANSPOSE)
@@ -420,6 +430,7 @@ static kg_status qf_eval_t(kg_problem* p, const void* x, void* f, T* y, cudaStre
 
 kg_status qf_eval(kg_problem* p, const void* x, void* f, cudaStream_t s) {
   if (p->arith == KG_ARITH_PAIR) return qf_pair_eval(p, x, f, s);
+  if (p->qf.streamed) return qf_f32_eval(p, x, f, s);
   return p->dtype == KG_F64 ? qf_eval_t<double>(p, x, f, nullptr, s)
                             : qf_eval_t<float>(p, x, f, nullptr, s);
 }
@@ -523,6 +534,12 @@ kg_status qf_grad(kg_problem* p, const void* x, void* f, void* gx, void* gA, con
       return fail(KG_ERR_UNSUPPORTED, "QUADFORM: the gradient w.r.t. A is produced by the native "
                                       "kernels (create the problem with KG_ARITH_NATIVE)");
     return qf_pair_grad(p, x, f, gx, seed, accumulate, s);
+  }
+  if (p->qf.streamed) {
+    if (gA)
+      return fail(KG_ERR_UNSUPPORTED, "QUADFORM: the gradient w.r.t. A is produced by the register "
+                                      "team kernels (pass team=block size)");
+    return qf_f32_grad(p, x, f, gx, seed, accumulate, s);
   }
   return p->dtype == KG_F64 ? qf_grad_t<double>(p, x, f, gx, gA, seed, accumulate, s)
                             : qf_grad_t<float>(p, x, f, gx, gA, seed, accumulate, s);
