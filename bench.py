@@ -178,10 +178,15 @@ class DenseWL(Workload):
         return self.es * self.n, self.es * (self.n + 1)
 
     def config(self):
-        return {"workload": f"dense ||Ax||^2, A {self.m}x{self.n} {self.dtype.upper()} "
-                            f"({self.es * self.m * self.n / 1e6:.0f} MB), value+grad wrt x",
-                "strategy": self.strategy, "arith": self.arith,
-                "l2": "inputs larger than L2 (A > 129 MB)"}
+        cfg = {"workload": f"dense ||Ax||^2, A {self.m}x{self.n} {self.dtype.upper()} "
+                           f"({self.es * self.m * self.n / 1e6:.0f} MB), value+grad wrt x",
+               "strategy": self.strategy, "arith": self.arith,
+               "l2": "inputs larger than L2 (A > 129 MB)"}
+        if getattr(self, "p", None) is not None and self.dtype == "f64" and \
+                self.p.workspace_bytes >= 8 * self.m * self.n:
+            cfg["A_layout"] = ("float pairs (hi, lo) prepared once by kg_create, 8 B per entry "
+                               "as in FP64; eval and grad stream that copy")
+        return cfg
 
     def oracle_sample(self, budget_s=10.0):
         from oracle import oracle as O
@@ -199,7 +204,7 @@ class DenseWL(Workload):
 
 
 class TetWL(Workload):
-    def __init__(self, a, dtype, strategy="atomic", arith="auto"):
+    def __init__(self, a, dtype, strategy="auto", arith="auto"):
         self.a = a
         self.dtype = dtype
         self.dtype_name = dtype
@@ -532,7 +537,7 @@ class AutogradWL(Workload):
                                            f"scaled to the full mesh (oracle, 1 thread)")
 
 
-def make_workload(name: str, arith: str, size: int = 0, rows: int = 0):
+def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy: str = ""):
     if name == "autograd":
         return AutogradWL(size or 100, "f64", arith=arith)
     if name == "autograd32":
@@ -546,9 +551,9 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0):
     if name == "dense64":
         return DenseWL(64, "f64", arith=arith)
     if name == "tet":
-        return TetWL(size or 100, "f64", arith=arith)
+        return TetWL(size or 100, "f64", strategy=strategy or "auto", arith=arith)
     if name == "tet32":
-        return TetWL(size or 100, "f32")
+        return TetWL(size or 100, "f32", strategy=strategy or "auto")
     if name == "tetcsr":
         return TetWL(size or 100, "f64", strategy="csr", arith=arith)
     if name == "laplace":
@@ -588,6 +593,8 @@ def main():
                     help="problem size override (dense n, tet cubes per axis, 1-D n) for small "
                          "profiling cases; the default is the full workload")
     ap.add_argument("--rows", type=int, default=0, help="dense: rows of A (default: square)")
+    ap.add_argument("--strategy", default="", choices=["", "atomic", "shared", "csr"],
+                    help="tet: reverse-pass strategy (default: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -615,7 +622,7 @@ def main():
         B.build()
     if dist:
         dist.barrier()
-    wl = make_workload(args.workload, args.arith, args.size, args.rows)
+    wl = make_workload(args.workload, args.arith, args.size, args.rows, args.strategy)
     wl.setup(dev)
     stream = torch.cuda.current_stream()
     peaks = load_peaks()

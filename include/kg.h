@@ -33,7 +33,9 @@
  *     KG_F32); index arrays are int32.  Scalars such as f and the seed are
  *     single elements of that dtype, in device memory.
  *   - Inputs given to kg_create (A, conn, G, b) are BORROWED: the caller owns
- *     them and keeps them alive and unchanged-in-shape until kg_destroy.
+ *     them and keeps them alive and unchanged until kg_destroy (kg_create
+ *     scans them and may derive prepared copies from them, see
+ *     tape_budget_bytes).
  *     All workspaces (partial sums, tape, transposed connectivity, error word)
  *     are allocated by kg_create / kg_batch_create; the per-call entry points
  *     kg_eval, kg_grad, kg_eval_tape, kg_grad_from_tape and kg_grad_batched
@@ -86,13 +88,19 @@ typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
  *   FUSED     (dense) one pass over A: each team computes y_i, broadcasts
  *             ybar_i and accumulates ybar_i A_i,: into private partials that a
  *             second tiny kernel sums in a fixed order; reproducible.
- *   AUTO      FUSED for dense, ATOMIC for tets, the stencil transpose for 1-D. */
+ *   SHARED    (tet) the forward schedule with the scatter-adds of each tile of
+ *             elements first combined per vertex in a shared-memory table, then
+ *             one global atomic per distinct vertex (Sec. 5: shared memory for
+ *             temporaries to reduce atomics).
+ *   AUTO      FUSED for dense, ATOMIC for FP64 tets, SHARED for FP32 tets, the
+ *             stencil transpose for 1-D. */
 typedef enum {
   KG_STRATEGY_AUTO = 0,
   KG_STRATEGY_ATOMIC = 1,
   KG_STRATEGY_CSR = 2,
   KG_STRATEGY_TRANSPOSE = 3,
-  KG_STRATEGY_FUSED = 4
+  KG_STRATEGY_FUSED = 4,
+  KG_STRATEGY_SHARED = 5
 } kg_strategy;
 
 /* Forward values for the reverse pass (Sec. 5, taping restriction).
@@ -123,7 +131,11 @@ typedef struct {
   int block;                /* threads per CTA; 0 = tuned default */
   int team;                 /* dense: threads per row team (32 or block); 0 = tuned */
   int tile;                 /* elements (tet) or rows (dense) per work tile; 0 = tuned */
-  size_t tape_budget_bytes; /* cap for KG_MODE_AUTO; 0 = 1 GiB */
+  size_t tape_budget_bytes; /* cap on optional create-time workspaces; 0 = 1 GiB:
+                             * the tet tape in KG_MODE_AUTO, and for FP64
+                             * QUADFORM in PAIR arithmetic a copy of A split into
+                             * float pairs (8 m n bytes) that the kernels then
+                             * stream instead of splitting A on every call */
 } kg_options;
 
 typedef struct kg_problem kg_problem;

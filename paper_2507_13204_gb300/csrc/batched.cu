@@ -307,10 +307,10 @@ __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, co
     if constexpr (PAIR) {
       elem_pair<TS_GRAD>(c, reinterpret_cast<const double*>(G) + e * 12,
                          reinterpret_cast<const double*>(u), Pair{2.0f, 0.0f}, tab, K, fp,
-                         reinterpret_cast<double*>(gu), nullptr, bad);
+                         AtomicSink<double>{reinterpret_cast<double*>(gu)}, nullptr, bad);
       if ((cnt & 31) == 31) acc_renorm(fp);
     } else {
-      elem_native<T, TS_GRAD>(c, G + e * 12, u, T(1), fn, gu, nullptr);
+      elem_native<T, TS_GRAD>(c, G + e * 12, u, T(1), fn, AtomicSink<T>{gu}, nullptr);
     }
   }
   __syncthreads();

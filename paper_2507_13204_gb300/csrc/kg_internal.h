@@ -68,6 +68,7 @@ struct kg_problem {
   unsigned* err = nullptr;   // sticky error word
   void* y = nullptr;         // dense / 1-D: forward intermediates
   void* tape = nullptr;      // tet: c_e [N_e][4]
+  void* aprep = nullptr;     // dense FP64 pair: A split into float pairs (m*n float2)
   bool tape_valid = false;
   int* rowptr = nullptr;     // tet CSR: [N_v + 1]
   int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k
@@ -102,6 +103,7 @@ kg_status qf_f32_grad(kg_problem* p, const void* x, void* f, void* gx, const voi
 bool qf_pair_supported(const kg_problem* p);
 kg_status pair_range_ok(kg_problem* p, const double* data, int64_t count, cudaStream_t s, bool* ok);
 kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok);
+kg_status qf_pair_prepare(kg_problem* p, cudaStream_t s);
 int qf_pair_grid(const kg_problem* p, int* band);
 kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,

@@ -2,6 +2,12 @@
 // batched persistent kernel: native (FP32 / FP64 instructions) and float-pair
 // (FP64 data) variants of g_e = G_e u_e, f_e = log1p(|g_e|^2) and the reverse
 // c_e = G_e^T (2 fbar g_e / (1 + |g_e|^2)) with its scatter-add or tape store.
+//
+// The scatter-add goes through a sink: AtomicSink adds straight into gu in
+// global memory; HashSink first combines the contributions of a tile of
+// elements per vertex in a shared-memory open-addressing table (Sec. 5:
+// shared memory for temporaries), which hash_flush then adds into gu with one
+// global atomic per distinct vertex.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,15 +27,63 @@ __device__ __forceinline__ Acc shfl_xor_acc2(Acc a, int o) {
 }
 
 template <typename T>
+struct AtomicSink {
+  T* gu;
+  __device__ __forceinline__ void operator()(int v, T c) const { atomicAdd(gu + v, c); }
+};
+
+// Per-tile table of (vertex, partial sum) in shared memory.  keys[] holds -1
+// for an empty slot.  Insertion probes linearly from a multiplicative hash;
+// a slot is claimed with atomicCAS and the value added with a shared atomic.
+// A tile inserts at most 4 x (elements per tile) distinct vertices, fewer than
+// SLOTS, so a free slot always exists; the global atomic after the probe loop
+// only keeps the sink total if that bound were ever broken.
+template <typename T, int SLOTS>
+struct HashSink {
+  int* keys;
+  T* vals;
+  T* gu;
+  __device__ __forceinline__ void operator()(int v, T c) const {
+    static_assert((SLOTS & (SLOTS - 1)) == 0, "SLOTS must be a power of two");
+    unsigned h = ((unsigned)v * 2654435761u) >> (32 - __builtin_ctz(SLOTS));
+    for (int probe = 0; probe < SLOTS; ++probe) {
+      int k = reinterpret_cast<volatile int*>(keys)[h];
+      if (k == -1) k = atomicCAS(keys + h, -1, v);
+      if (k == -1 || k == v) {
+        atomicAdd(vals + h, c);
+        return;
+      }
+      h = (h + 1) & (SLOTS - 1);
+    }
+    atomicAdd(gu + v, c);
+  }
+};
+
+// Adds every occupied slot into gu and empties the table (all threads of the
+// CTA, after a barrier that ends the tile's insertions).
+template <typename T, int SLOTS, int THREADS>
+__device__ __forceinline__ void hash_flush(int* keys, T* vals, T* gu, int tid) {
+#pragma unroll
+  for (int j = tid; j < SLOTS; j += THREADS) {
+    const int k = keys[j];
+    if (k != -1) {
+      atomicAdd(gu + k, vals[j]);
+      keys[j] = -1;
+      vals[j] = T(0);
+    }
+  }
+}
+
+template <typename T>
 __device__ __forceinline__ T log1p_nat(T v) {
   if constexpr (sizeof(T) == 8) return log1p(v);
   else return log1pf(v);
 }
 
 // One element in native arithmetic (T = float or double).
-template <typename T, int MODE>
+template <typename T, int MODE, typename Sink>
 __device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ Gs,
-                                            const T* __restrict__ u, T fb, T& facc, T* gu,
+                                            const T* __restrict__ u, T fb, T& facc, const Sink& gu,
                                             T* tape_e) {
   T G[12];
 #pragma unroll
@@ -48,10 +102,10 @@ __device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ 
     const T c2 = G[2] * w0 + G[6] * w1 + G[10] * w2;
     const T c3 = G[3] * w0 + G[7] * w1 + G[11] * w2;
     if constexpr (MODE == TS_GRAD) {
-      atomicAdd(gu + c.x, c0);
-      atomicAdd(gu + c.y, c1);
-      atomicAdd(gu + c.z, c2);
-      atomicAdd(gu + c.w, c3);
+      gu(c.x, c0);
+      gu(c.y, c1);
+      gu(c.z, c2);
+      gu(c.w, c3);
     } else {
       tape_e[0] = c0;
       tape_e[1] = c1;
@@ -62,11 +116,11 @@ __device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ 
 }
 
 // One element in float-pair arithmetic (FP64 data).
-template <int MODE>
+template <int MODE, typename Sink>
 __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict__ Gs,
                                           const double* __restrict__ u, Pair fb2,
                                           const float4* __restrict__ tab, const LogConsts& K,
-                                          Acc& facc, double* gu, double* tape_e, bool& bad) {
+                                          Acc& facc, const Sink& gu, double* tape_e, bool& bad) {
   Pair G[12];
 #pragma unroll
   for (int i = 0; i < 12; i += 2) {
@@ -110,10 +164,10 @@ __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict
       cd[k] = pair_to_double_fast(acc_pair(a));
     }
     if constexpr (MODE == TS_GRAD) {
-      atomicAdd(gu + c.x, cd[0]);
-      atomicAdd(gu + c.y, cd[1]);
-      atomicAdd(gu + c.z, cd[2]);
-      atomicAdd(gu + c.w, cd[3]);
+      gu(c.x, cd[0]);
+      gu(c.y, cd[1]);
+      gu(c.z, cd[2]);
+      gu(c.w, cd[3]);
     } else {
       reinterpret_cast<double2*>(tape_e)[0] = make_double2(cd[0], cd[1]);
       reinterpret_cast<double2*>(tape_e)[1] = make_double2(cd[2], cd[3]);

@@ -13,6 +13,10 @@
 //     doubles into float pairs (integer instructions), writes the split values
 //     back in place so the reverse pass does not split again, and accumulates
 //     with FMA two-product / TwoSum on the FP32 units;
+//   - PREP: when the problem holds A already split into float pairs (made once
+//     by kg_create, same 8 bytes per entry), rows of that copy stream instead
+//     and no split or write-back runs in the row loop (about a fifth of the
+//     instructions per entry);
 //   - the private xbar partials (float pairs) of each CTA go to a workspace that
 //     a second kernel sums in a fixed order: bitwise reproducible.
 // All waits are bounded (about one second) and report KG_ERR_TIMEOUT.
@@ -33,7 +37,7 @@ constexpr int QP_THREADS = QP_CT;
 constexpr int QP_BAR = 1;                    // named barrier id
 
 struct QpArgs {
-  const double* A;
+  const double* A;   // FP64 rows, or (PREP) rows of float pairs (h0, l0, h1, l1, ...)
   const double* x;
   int64_t m;
   int n;  // even
@@ -53,7 +57,7 @@ __device__ __forceinline__ Acc shfl_xor_acc(Acc a, int o) {
   return b;
 }
 
-template <int PPT, bool FUSED>
+template <int PPT, bool FUSED, bool PREP>
 __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int n = a.n, npairs = n >> 1;
@@ -128,9 +132,17 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
       for (int k = 0; k < PPT; ++k) {
         const int jp = t + QP_CT * k;
         if (jp < npairs) {
-          const double2 v = rowd[jp];
-          const Pair p0 = split_f64(v.x), p1 = split_f64(v.y);
-          if (FUSED) rowf[jp] = make_float4(p0.h, p0.l, p1.h, p1.l);
+          Pair p0, p1;
+          if (PREP) {
+            const float4 q = rowf[jp];
+            p0 = Pair{q.x, q.y};
+            p1 = Pair{q.z, q.w};
+          } else {
+            const double2 v = rowd[jp];
+            p0 = split_f64(v.x);
+            p1 = split_f64(v.y);
+            if (FUSED) rowf[jp] = make_float4(p0.h, p0.l, p1.h, p1.l);
+          }
           acc_fma(yc[2 * (k & 1)], p0.h, p0.l, xh[k][0], xl[k][0]);
           acc_fma(yc[2 * (k & 1) + 1], p1.h, p1.l, xh[k][1], xl[k][1]);
         }
@@ -175,7 +187,7 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
           acc_renorm(xb[k][1]);
         }
       }
-      fence_proxy_async_smem();  // split values were written with generic stores
+      if (!PREP) fence_proxy_async_smem();  // split values were written with generic stores
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
@@ -289,6 +301,17 @@ __global__ void __launch_bounds__(512) qf_pair_reduce_kernel(const float4* __res
   }
 }
 
+// The prepared copy of A: every double split into its float pair (h, l).
+__global__ void pair_prepare_kernel(const double2* __restrict__ A, float4* __restrict__ out,
+                                    int64_t n2) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+    const double2 v = __ldcs(A + i);
+    const Pair p0 = split_f64(v.x), p1 = split_f64(v.y);
+    __stcs(out + i, make_float4(p0.h, p0.l, p1.h, p1.l));
+  }
+}
+
 // Sets ERRBIT_RANGE when some entry is outside the pair arithmetic's range.
 __global__ void pair_range_scan_kernel(const double2* __restrict__ p, int64_t n2, unsigned* err) {
   bool bad = false;
@@ -348,32 +371,55 @@ int qf_pair_grid(const kg_problem* p, int* band) {
   return (int)((p->m + b - 1) / b);
 }
 
-template <int PPT, bool FUSED>
+template <int PPT, bool FUSED, bool PREP>
 static cudaError_t launch_pair(int grid, size_t smem, cudaStream_t s, const QpArgs& a) {
-  auto kern = qf_pair_kernel<PPT, FUSED>;
+  auto kern = qf_pair_kernel<PPT, FUSED, PREP>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, QP_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-template <bool FUSED>
-static cudaError_t dispatch_pair(int ppt, int grid, size_t smem, cudaStream_t s, const QpArgs& a) {
+template <bool FUSED, bool PREP>
+static cudaError_t dispatch_ppt(int ppt, int grid, size_t smem, cudaStream_t s, const QpArgs& a) {
   switch (ppt) {
-    case 1: return launch_pair<1, FUSED>(grid, smem, s, a);
-    case 2: return launch_pair<2, FUSED>(grid, smem, s, a);
-    case 4: return launch_pair<4, FUSED>(grid, smem, s, a);
-    case 6: return launch_pair<6, FUSED>(grid, smem, s, a);
-    case 8: return launch_pair<8, FUSED>(grid, smem, s, a);
-    case 10: return launch_pair<10, FUSED>(grid, smem, s, a);
-    case 12: return launch_pair<12, FUSED>(grid, smem, s, a);
+    case 1: return launch_pair<1, FUSED, PREP>(grid, smem, s, a);
+    case 2: return launch_pair<2, FUSED, PREP>(grid, smem, s, a);
+    case 4: return launch_pair<4, FUSED, PREP>(grid, smem, s, a);
+    case 6: return launch_pair<6, FUSED, PREP>(grid, smem, s, a);
+    case 8: return launch_pair<8, FUSED, PREP>(grid, smem, s, a);
+    case 10: return launch_pair<10, FUSED, PREP>(grid, smem, s, a);
+    case 12: return launch_pair<12, FUSED, PREP>(grid, smem, s, a);
   }
   return cudaErrorInvalidValue;
 }
 
+template <bool FUSED>
+static cudaError_t dispatch_pair(bool prep, int ppt, int grid, size_t smem, cudaStream_t s,
+                                 const QpArgs& a) {
+  return prep ? dispatch_ppt<FUSED, true>(ppt, grid, smem, s, a)
+              : dispatch_ppt<FUSED, false>(ppt, grid, smem, s, a);
+}
+
+// Prepared copy of A (float pairs, 8 bytes per entry) when it fits the
+// problem's workspace budget; later calls stream it instead of A.
+kg_status qf_pair_prepare(kg_problem* p, cudaStream_t s) {
+  const size_t bytes = 8 * (size_t)p->m * (size_t)p->n;
+  const size_t budget = p->opt.tape_budget_bytes ? p->opt.tape_budget_bytes : (size_t(1) << 30);
+  if (bytes > budget) return KG_OK;
+  kg_status rc = ws_alloc(p, &p->aprep, bytes, "prepared A (float pairs)");
+  if (rc != KG_OK) return rc;
+  const int64_t n2 = (int64_t)p->m * p->n / 2;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n2 + 255) / 256, (int64_t)num_sms() * 8));
+  pair_prepare_kernel<<<grid, 256, 0, s>>>(static_cast<const double2*>(p->data0),
+                                           static_cast<float4*>(p->aprep), n2);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KG_OK : cuda_fail(e, "prepare A");
+}
+
 static QpArgs pair_args(kg_problem* p, const void* x, const void* seed) {
   QpArgs a{};
-  a.A = static_cast<const double*>(p->data0);
+  a.A = static_cast<const double*>(p->aprep ? p->aprep : p->data0);
   a.x = static_cast<const double*>(x);
   a.m = p->m;
   a.n = (int)p->n;
@@ -391,8 +437,9 @@ kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s) {
     return fail(KG_ERR_INVALID_ARG, "QUADFORM pair kernels need a 16-byte aligned x");
   QpArgs a = pair_args(p, x, nullptr);
   a.f = static_cast<double*>(f);
-  prof_begin(s, "qf_pair_kernel<eval>");
-  cudaError_t e = dispatch_pair<false>(pair_ppt(p->n), p->qf.grid, pair_smem((int)p->n), s, a);
+  prof_begin(s, p->aprep ? "qf_pair_kernel<eval, prepared A>" : "qf_pair_kernel<eval>");
+  cudaError_t e = dispatch_pair<false>(p->aprep != nullptr, pair_ppt(p->n), p->qf.grid,
+                                       pair_smem((int)p->n), s, a);
   prof_end(s);
   count_launch();
   return e == cudaSuccess ? KG_OK : cuda_fail(e, "qf pair forward kernel");
@@ -403,8 +450,9 @@ kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const vo
   if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0 || (reinterpret_cast<uintptr_t>(gx) & 15u) != 0)
     return fail(KG_ERR_INVALID_ARG, "QUADFORM pair kernels need 16-byte aligned x and gx");
   QpArgs a = pair_args(p, x, seed);
-  prof_begin(s, "qf_pair_kernel<fused>");
-  cudaError_t e = dispatch_pair<true>(pair_ppt(p->n), p->qf.grid, pair_smem((int)p->n), s, a);
+  prof_begin(s, p->aprep ? "qf_pair_kernel<fused, prepared A>" : "qf_pair_kernel<fused>");
+  cudaError_t e = dispatch_pair<true>(p->aprep != nullptr, pair_ppt(p->n), p->qf.grid,
+                                      pair_smem((int)p->n), s, a);
   prof_end(s);
   count_launch();
   if (e != cudaSuccess) return cuda_fail(e, "qf pair fused kernel");

@@ -144,9 +144,11 @@ static int grid_for(int64_t work, int block, int per_sm) {
 kg_status tet_setup(kg_problem* p, cudaStream_t s) {
   if (p->m * 4 >= (int64_t(1) << 31))
     return fail(KG_ERR_INVALID_ARG, "TETENERGY: 4 * N_e must be < 2^31");
-  if (p->strategy == KG_STRATEGY_AUTO) p->strategy = KG_STRATEGY_ATOMIC;
-  if (p->strategy != KG_STRATEGY_ATOMIC && p->strategy != KG_STRATEGY_CSR)
-    return fail(KG_ERR_UNSUPPORTED, "TETENERGY: strategy must be ATOMIC or CSR");
+  if (p->strategy == KG_STRATEGY_AUTO)
+    p->strategy = p->dtype == KG_F32 ? KG_STRATEGY_SHARED : KG_STRATEGY_ATOMIC;
+  if (p->strategy != KG_STRATEGY_ATOMIC && p->strategy != KG_STRATEGY_CSR &&
+      p->strategy != KG_STRATEGY_SHARED)
+    return fail(KG_ERR_UNSUPPORTED, "TETENERGY: strategy must be ATOMIC, SHARED or CSR");
   const size_t tape_bytes = p->esize * 4 * (size_t)p->m;
   const size_t budget = p->opt.tape_budget_bytes ? p->opt.tape_budget_bytes : (size_t(1) << 30);
   if (p->mode == KG_MODE_AUTO) p->mode = tape_bytes <= budget ? KG_MODE_TAPE : KG_MODE_RECOMPUTE;

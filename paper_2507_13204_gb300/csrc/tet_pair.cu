@@ -10,6 +10,13 @@
 // reverse modes, c_e = G_e^T (2 fbar g_e / (1 + |g_e|^2)), which it either
 // scatter-adds into gu (FP64/FP32 atomics) or stores to the tape.
 //
+// KG_STRATEGY_SHARED: the scatter-adds of a tile are first combined per vertex
+// in a shared-memory hash table (two tables, used by alternate tiles); after
+// one CTA barrier per tile the table is added into gu with one global atomic
+// per distinct vertex and emptied.  With elements numbered along the mesh a
+// tile of 256 tets of the Kuhn grid touches ~180 distinct vertices for its
+// 1024 contributions, so global atomics drop ~5x.
+//
 // Arithmetic: FP32 for FP32 problems; for FP64 problems either native FP64
 // or float pairs (kg_pair.cuh) with the results converted back to double for
 // the atomics / tape (KG_ARITH_PAIR: GB300's FP64 units are ~60x slower than
@@ -18,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <mutex>
 #include <string>
 
@@ -31,6 +39,10 @@ namespace kg {
 constexpr int TS_THREADS = 256;  // threads per CTA == elements per tile
 constexpr int TS_WARPS = TS_THREADS / 32;
 constexpr int TS_STAGES = 2;
+
+// Slots of one shared-memory aggregation table (power of two, > 4 x TS_THREADS).
+template <typename T>
+__host__ __device__ constexpr int ts_hash_slots() { return 2048; }
 
 
 template <typename T>
@@ -52,7 +64,7 @@ struct TsArgs {
   LogConsts K;
 };
 
-template <typename T, bool PAIR, int MODE>
+template <typename T, bool PAIR, int MODE, bool SHARED>
 __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr uint32_t kConnBytes = TS_THREADS * 16u;
@@ -63,6 +75,10 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
   float4* tab = reinterpret_cast<float4*>(empty + TS_STAGES);  // PAIR only
   double* red = reinterpret_cast<double*>(tab + (PAIR ? kLogTableSize : 0));
   volatile int* abort_flag = reinterpret_cast<volatile int*>(red + 2 * TS_WARPS);
+  constexpr int kSlots = ts_hash_slots<T>();
+  // SHARED: tables [2][kSlots] of values, then [2][kSlots] of keys
+  T* hvals = reinterpret_cast<T*>(red + 2 * TS_WARPS + 2);
+  int* hkeys = reinterpret_cast<int*>(hvals + (SHARED ? 2 * kSlots : 0));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t ntiles = (a.ne + TS_THREADS - 1) / TS_THREADS;
@@ -78,6 +94,12 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
   }
   if constexpr (PAIR) {
     for (int i = tid; i < kLogTableSize; i += TS_THREADS) tab[i] = a.logtab[i];
+  }
+  if constexpr (SHARED) {
+    for (int i = tid; i < 2 * kSlots; i += TS_THREADS) {
+      hkeys[i] = -1;
+      hvals[i] = T(0);
+    }
   }
   __syncthreads();
 
@@ -132,15 +154,25 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
         if (!inb) set_error(a.err, ERRBIT_BOUNDS);
       }
       if (inb) {
-        if constexpr (PAIR) {
-          elem_pair<MODE>(c, reinterpret_cast<const double*>(Gs), reinterpret_cast<const double*>(a.u),
-                          fb2, tab, a.K, facc_p, reinterpret_cast<double*>(a.gu),
-                          reinterpret_cast<double*>(a.tape) + e * 4, bad);
-          if ((i & 31) == 31) acc_renorm(facc_p);
-        } else {
-          elem_native<T, MODE>(c, Gs, a.u, fb, facc_n, a.gu, a.tape + e * 4);
-        }
+        const int tb = (int)(i & 1) * kSlots;
+        auto run = [&](const auto& sink) {
+          if constexpr (PAIR) {
+            elem_pair<MODE>(c, reinterpret_cast<const double*>(Gs),
+                            reinterpret_cast<const double*>(a.u), fb2, tab, a.K, facc_p, sink,
+                            reinterpret_cast<double*>(a.tape) + e * 4, bad);
+            if ((i & 31) == 31) acc_renorm(facc_p);
+          } else {
+            elem_native<T, MODE>(c, Gs, a.u, fb, facc_n, sink, a.tape + e * 4);
+          }
+        };
+        if constexpr (SHARED) run(HashSink<T, kSlots>{hkeys + tb, hvals + tb, a.gu});
+        else run(AtomicSink<T>{a.gu});
       }
+    }
+    if constexpr (SHARED) {  // the tile's insertions are complete: add the table into gu
+      __syncthreads();
+      const int tb = (int)(i & 1) * kSlots;
+      hash_flush<T, kSlots, TS_THREADS>(hkeys + tb, hvals + tb, a.gu, tid);
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[s]);
@@ -227,16 +259,43 @@ kg_status logtab_for_device(const float4** out) {
   return KG_OK;
 }
 
-template <typename T, bool PAIR>
+template <typename T, bool PAIR, bool SHARED>
 static size_t ts_smem() {
   return (size_t)TS_STAGES * (TS_THREADS * 16 + TS_THREADS * 12 * sizeof(T)) +
          2 * TS_STAGES * sizeof(uint64_t) + (PAIR ? kLogTableSize * sizeof(float4) : 0) +
-         2 * TS_WARPS * sizeof(double) + 16;
+         (2 * TS_WARPS + 2) * sizeof(double) +
+         (SHARED ? 2 * (size_t)ts_hash_slots<T>() * (sizeof(T) + sizeof(int)) : 0);
 }
+
+// Upper bound of the staged kernels' grids (the f partials are sized for it):
+// up to TS_MAX_PER_SM CTAs per SM.  Each launch takes the occupancy of its own
+// kernel (registers, shared memory) within that bound.
+constexpr int TS_MAX_PER_SM = 6;
 
 int tet_staged_grid(const kg_problem* p) {
   const int64_t ntiles = (p->m + TS_THREADS - 1) / TS_THREADS;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * 3));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * TS_MAX_PER_SM));
+}
+
+static int ts_cap() {
+  static const int v = [] { const char* e = getenv("KG_TET_CAP"); return e ? atoi(e) : 0; }();
+  return v;
+}
+
+// `occ` caches the kernel's resident CTAs per SM (queried on first use).
+template <typename K>
+static int ts_grid_for(const kg_problem* p, K kern, size_t smem, int& occ_cache) {
+  if (occ_cache < 1) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, kern, TS_THREADS, smem) != cudaSuccess)
+      o = 1;
+    occ_cache = std::max(o, 1);
+  }
+  int occ = occ_cache;
+  if (ts_cap() > 0) occ = std::min(occ, ts_cap());
+  const int64_t ntiles = (p->m + TS_THREADS - 1) / TS_THREADS;
+  const int64_t g = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::min(occ, TS_MAX_PER_SM));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, p->tet_grid));
 }
 
 kg_status tet_staged_setup(kg_problem* p) {
@@ -250,11 +309,24 @@ kg_status tet_staged_setup(kg_problem* p) {
 
 template <typename T, bool PAIR, int MODE>
 static cudaError_t launch_ts(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
-  auto kern = tet_staged_kernel<T, PAIR, MODE>;
-  const size_t smem = ts_smem<T, PAIR>();
+  if constexpr (MODE == TS_GRAD) {
+    if (p->strategy == KG_STRATEGY_SHARED) {
+      auto kern = tet_staged_kernel<T, PAIR, MODE, true>;
+      const size_t smem = ts_smem<T, PAIR, true>();
+      cudaError_t e =
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      static int occ = 0;
+      kern<<<ts_grid_for(p, kern, smem, occ), TS_THREADS, smem, s>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  auto kern = tet_staged_kernel<T, PAIR, MODE, false>;
+  const size_t smem = ts_smem<T, PAIR, false>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  kern<<<p->tet_grid, TS_THREADS, smem, s>>>(a);
+  static int occ = 0;
+  kern<<<ts_grid_for(p, kern, smem, occ), TS_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 

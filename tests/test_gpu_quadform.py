@@ -124,6 +124,31 @@ def test_pair_and_native_arithmetic_both_match(api, m, n):
         p.close()
 
 
+@pytest.mark.parametrize("m,n", [(10000, 10000), (333, 1024), (5, 12288), (1000, 4098)])
+def test_prepared_and_on_the_fly_split_agree(api, m, n):
+    # within the workspace budget kg_create keeps A split into float pairs and the kernels
+    # stream that copy; a budget below 8 m n bytes makes them split A on every call.  The
+    # split is the same function either way, so both give bitwise identical results.
+    A, x = W.quadform_inputs(n, m=m, seed=n + 2 * m)
+    f_ref, g_ref = O.quadform_grad(A, x)
+    At, xt = torch.tensor(A, device="cuda"), torch.tensor(x, device="cuda")
+    prep = api.QuadForm(At)
+    fly = api.QuadForm(At, tape_budget_bytes=8 * m * n - 8)
+    assert prep.config[2] == fly.config[2] == "pair"
+    assert prep.workspace_bytes - fly.workspace_bytes == 8 * m * n
+    out = []
+    for p in (prep, fly):
+        f, g = p.grad(xt)
+        fe = p.eval(xt)
+        p.sync()
+        assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+        assert rel_scalar(fe.item(), f_ref) <= TOL["f64"]
+        assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+        out.append((f.clone(), g.clone(), fe.clone()))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
+
+
 def test_pair_is_default_for_f64_and_reproducible(api):
     A, x = W.quadform_inputs(2048, m=700, seed=4)
     p = api.QuadForm(torch.tensor(A, device="cuda"))

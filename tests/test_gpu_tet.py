@@ -1,5 +1,6 @@
-"""GPU parity: tet-mesh energy value and gradient (atomic scatter and CSR gather,
-recompute and tape) through the C ABI vs the CPU oracle."""
+"""GPU parity: tet-mesh energy value and gradient (atomic scatter, shared-memory
+aggregated scatter and CSR gather; recompute and tape) through the C ABI vs the
+CPU oracle."""
 import numpy as np
 import pytest
 import torch
@@ -29,7 +30,7 @@ MESHES = [(1, None), (3, 2), (7, None), (12, 2), (25, 2)]
 
 
 @pytest.mark.parametrize("a,jit", MESHES)
-@pytest.mark.parametrize("strategy", ["atomic", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "csr"])
 def test_f64_grad_matches_oracle(api, a, jit, strategy):
     mesh = W.tet_mesh(a, jitter_seed=jit, perm_seed=a)
     u = np.random.default_rng(a).uniform(-1, 1, mesh.nv)
@@ -44,7 +45,7 @@ def test_f64_grad_matches_oracle(api, a, jit, strategy):
     assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
 
 
-@pytest.mark.parametrize("strategy", ["atomic", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "csr"])
 def test_f32_matches_oracle_on_rounded_inputs(api, strategy):
     mesh = W.tet_mesh(20, jitter_seed=2, perm_seed=3)
     u = np.random.default_rng(5).uniform(-1, 1, mesh.nv)
@@ -59,7 +60,7 @@ def test_f32_matches_oracle_on_rounded_inputs(api, strategy):
     assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f32"]
 
 
-@pytest.mark.parametrize("strategy", ["atomic", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "csr"])
 def test_tape_mode_seed_and_accumulate(api, strategy):
     mesh = W.tet_mesh(9, jitter_seed=2, perm_seed=4)
     u = np.random.default_rng(6).uniform(-1, 1, mesh.nv)
@@ -119,7 +120,7 @@ def test_full_size_100_cubed_f64(api):
     mesh, u = W.tet_inputs(100)
     f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
     ut = torch.tensor(u, device="cuda")
-    for strategy in ("atomic", "csr"):
+    for strategy in ("atomic", "shared", "csr"):
         p = _problem(api, mesh, torch.float64, strategy=strategy)
         f, g = p.grad(ut)
         fe = p.eval(ut)
@@ -155,7 +156,7 @@ def test_checked_kernels_flag_connectivity_changed_after_create(api):
 
 
 @pytest.mark.parametrize("arith", ["pair", "native"])
-@pytest.mark.parametrize("strategy", ["atomic", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "csr"])
 def test_pair_and_native_match_oracle_jittered(api, arith, strategy):
     mesh = W.tet_mesh(18, jitter_seed=2, perm_seed=5)
     u = np.random.default_rng(21).uniform(-1, 1, mesh.nv)
@@ -202,8 +203,38 @@ def test_ragged_tiles_and_tiny_meshes(api):
         u = np.random.default_rng(a * b * c).uniform(-1, 1, mesh.nv)
         f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
         for arith in ("pair", "native"):
-            p = _problem(api, mesh, torch.float64, arith=arith)
-            f, g = p.grad(torch.tensor(u, device="cuda"))
-            p.sync()
-            assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
-            assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+            for strategy in ("atomic", "shared"):
+                p = _problem(api, mesh, torch.float64, arith=arith, strategy=strategy)
+                f, g = p.grad(torch.tensor(u, device="cuda"))
+                p.sync()
+                assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+                assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_shared_aggregation_with_scattered_element_order(api, dtype):
+    # elements in random order: a 256-tet tile then touches ~1000 distinct vertices, close to
+    # the worst case for the shared-memory table (long probe chains, nearly no combining)
+    mesh = W.tet_mesh(14, jitter_seed=2, perm_seed=8)
+    order = np.random.default_rng(12).permutation(mesh.ne)
+    conn, G = np.ascontiguousarray(mesh.conn[order]), np.ascontiguousarray(mesh.G[order])
+    u = np.random.default_rng(13).uniform(-1, 1, mesh.nv)
+    if dtype == torch.float32:
+        G, u = f32_round(G), f32_round(u)
+    f_ref, g_ref = O.tet_grad(conn, G, u)
+    p = api.TetEnergy(torch.tensor(conn, device="cuda"), torch.tensor(G, dtype=dtype, device="cuda"),
+                      mesh.nv, strategy="shared")
+    assert p.config[0] == "shared"
+    f, g = p.grad(torch.tensor(u, dtype=dtype, device="cuda"))
+    p.sync()
+    tol = TOL["f64"] if dtype == torch.float64 else TOL["f32"]
+    assert rel_scalar(f.item(), f_ref) <= tol
+    assert rel_l2(g.cpu().numpy(), g_ref) <= tol
+
+
+def test_strategy_defaults(api):
+    mesh = W.tet_mesh(3)
+    conn = torch.tensor(mesh.conn, device="cuda")
+    p64 = api.TetEnergy(conn, torch.tensor(mesh.G, device="cuda"), mesh.nv)
+    p32 = api.TetEnergy(conn, torch.tensor(mesh.G, dtype=torch.float32, device="cuda"), mesh.nv)
+    assert p64.config[0] == "atomic" and p32.config[0] == "shared"
