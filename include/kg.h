@@ -131,11 +131,13 @@ typedef struct {
   int block;                /* threads per CTA; 0 = tuned default */
   int team;                 /* dense: threads per row team (32 or block); 0 = tuned */
   int tile;                 /* elements (tet) or rows (dense) per work tile; 0 = tuned */
-  size_t tape_budget_bytes; /* cap on optional create-time workspaces; 0 = 1 GiB:
-                             * the tet tape in KG_MODE_AUTO, and for FP64
-                             * QUADFORM in PAIR arithmetic a copy of A split into
-                             * float pairs (8 m n bytes) that the kernels then
-                             * stream instead of splitting A on every call */
+  size_t tape_budget_bytes; /* cap on optional create-time workspaces; 0 = 1 GiB.
+                             * FP64 problems in PAIR arithmetic first take a copy
+                             * of A (QUADFORM, 8 m n bytes) or G (TETENERGY,
+                             * 96 N_e bytes) split into float pairs, which the
+                             * kernels stream instead of splitting on every
+                             * call; KG_MODE_AUTO then takes the tet tape if it
+                             * fits what is left */
 } kg_options;
 
 typedef struct kg_problem kg_problem;

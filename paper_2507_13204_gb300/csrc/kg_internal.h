@@ -68,7 +68,7 @@ struct kg_problem {
   unsigned* err = nullptr;   // sticky error word
   void* y = nullptr;         // dense / 1-D: forward intermediates
   void* tape = nullptr;      // tet: c_e [N_e][4]
-  void* aprep = nullptr;     // dense FP64 pair: A split into float pairs (m*n float2)
+  void* aprep = nullptr;     // FP64 pair: A (dense) or G (tet) split into float pairs
   bool tape_valid = false;
   int* rowptr = nullptr;     // tet CSR: [N_v + 1]
   int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k
@@ -104,6 +104,8 @@ bool qf_pair_supported(const kg_problem* p);
 kg_status pair_range_ok(kg_problem* p, const double* data, int64_t count, cudaStream_t s, bool* ok);
 kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok);
 kg_status qf_pair_prepare(kg_problem* p, cudaStream_t s);
+// dst[i] = float pair (h, l) of src[i] for i < count (count even, 16-byte aligned)
+kg_status pair_prepare(const double* src, void* dst, int64_t count, cudaStream_t s);
 int qf_pair_grid(const kg_problem* p, int* band);
 kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,

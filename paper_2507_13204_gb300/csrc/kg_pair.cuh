@@ -5,7 +5,7 @@
 // (hi + lo):
 //   - split_f64 turns a double into hi (its leading 24 significant bits,
 //     truncated) and lo (the next 23 bits) with integer instructions only;
-//     the pair holds the double to within 2^-47 relative for
+//     the pair holds the double to within 2^-46 relative for
 //     2^-60 <= |d| < 2^40 (pair_in_range) and maps +-0 to +-0; callers check
 //     the range of their inputs.
 //   - products use the FMA error-free transformation: for floats a, b,
@@ -18,6 +18,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <math.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -194,8 +195,12 @@ __host__ __device__ __forceinline__ Pair pair_add(Pair a, Pair b) {
 // 1/t for t >= 1 (normalised pair): the correctly rounded float reciprocal r0
 // has relative error <= 2^-24; one Newton step r0 (1 + (1 - t r0)) in pair
 // form leaves an error of order 2^-48.
-__device__ __forceinline__ Pair pair_recip(Pair t) {
+__host__ __device__ __forceinline__ Pair pair_recip(Pair t) {
+#ifdef __CUDA_ARCH__
   const float r0 = __frcp_rn(t.h);
+#else
+  const float r0 = 1.0f / t.h;  // IEEE division: also correctly rounded
+#endif
   float e = fmaf(-t.h, r0, 1.0f);
   e = fmaf(-t.l, r0, e);
   Pair r;
@@ -259,16 +264,27 @@ __host__ __device__ __forceinline__ Pair pair_log1p(Pair s, const float4* __rest
   return pair_add(pair_add(el, Pair{T.x, T.y}), lp);
 }
 
+__host__ __device__ __forceinline__ double u64_to_f64(uint64_t u) {
+#ifdef __CUDA_ARCH__
+  return __longlong_as_double((long long)u);
+#else
+  double d;
+  memcpy(&d, &u, 8);
+  return d;
+#endif
+}
+
 // Exact float -> double with integer instructions (normal floats and zero).
-__device__ __forceinline__ double f32_to_f64_int(float f) {
+__host__ __device__ __forceinline__ double f32_to_f64_int(float f) {
   const uint32_t b = f2u(f);
   const uint32_t mag = b & 0x7FFFFFFFu;
   const uint32_t hi = (b & 0x80000000u) | (mag ? (mag >> 3) + (896u << 20) : 0u);
-  return __hiloint2double((int)hi, (int)(b << 29));
+  return u64_to_f64(((uint64_t)hi << 32) | (uint32_t)(b << 29));
 }
 
-// h + l as a double: two exact conversions on the integer units, one FP64 add.
-__device__ __forceinline__ double pair_to_double_fast(Pair p) {
+// h + l as a double: two exact conversions on the integer units, one FP64 add
+// (an all-integer add measured slower in the tet gradient kernel).
+__host__ __device__ __forceinline__ double pair_to_double_fast(Pair p) {
   return f32_to_f64_int(p.h) + f32_to_f64_int(p.l);
 }
 

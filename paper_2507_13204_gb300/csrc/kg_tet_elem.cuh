@@ -115,8 +115,9 @@ __device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ 
   }
 }
 
-// One element in float-pair arithmetic (FP64 data).
-template <int MODE, typename Sink>
+// One element in float-pair arithmetic (FP64 data).  Gs points at the
+// element's 12 doubles, or (PREP) at its 12 float pairs (h, l) prepared once.
+template <int MODE, typename Sink, bool PREP = false>
 __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict__ Gs,
                                           const double* __restrict__ u, Pair fb2,
                                           const float4* __restrict__ tab, const LogConsts& K,
@@ -124,9 +125,15 @@ __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict
   Pair G[12];
 #pragma unroll
   for (int i = 0; i < 12; i += 2) {
-    const double2 v = *reinterpret_cast<const double2*>(Gs + i);
-    G[i] = split_f64(v.x);
-    G[i + 1] = split_f64(v.y);
+    if constexpr (PREP) {
+      const float4 q = *reinterpret_cast<const float4*>(Gs + i);
+      G[i] = Pair{q.x, q.y};
+      G[i + 1] = Pair{q.z, q.w};
+    } else {
+      const double2 v = *reinterpret_cast<const double2*>(Gs + i);
+      G[i] = split_f64(v.x);
+      G[i + 1] = split_f64(v.y);
+    }
   }
   const double ud[4] = {__ldg(u + c.x), __ldg(u + c.y), __ldg(u + c.z), __ldg(u + c.w)};
   Pair U[4];

@@ -409,12 +409,16 @@ kg_status qf_pair_prepare(kg_problem* p, cudaStream_t s) {
   if (bytes > budget) return KG_OK;
   kg_status rc = ws_alloc(p, &p->aprep, bytes, "prepared A (float pairs)");
   if (rc != KG_OK) return rc;
-  const int64_t n2 = (int64_t)p->m * p->n / 2;
+  return pair_prepare(static_cast<const double*>(p->data0), p->aprep, (int64_t)p->m * p->n, s);
+}
+
+kg_status pair_prepare(const double* src, void* dst, int64_t count, cudaStream_t s) {
+  const int64_t n2 = count / 2;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n2 + 255) / 256, (int64_t)num_sms() * 8));
-  pair_prepare_kernel<<<grid, 256, 0, s>>>(static_cast<const double2*>(p->data0),
-                                           static_cast<float4*>(p->aprep), n2);
+  pair_prepare_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const double2*>(src),
+                                           static_cast<float4*>(dst), n2);
   cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? KG_OK : cuda_fail(e, "prepare A");
+  return e == cudaSuccess ? KG_OK : cuda_fail(e, "prepare float pairs");
 }
 
 static QpArgs pair_args(kg_problem* p, const void* x, const void* seed) {

@@ -150,16 +150,12 @@ kg_status tet_setup(kg_problem* p, cudaStream_t s) {
       p->strategy != KG_STRATEGY_SHARED)
     return fail(KG_ERR_UNSUPPORTED, "TETENERGY: strategy must be ATOMIC, SHARED or CSR");
   const size_t tape_bytes = p->esize * 4 * (size_t)p->m;
-  const size_t budget = p->opt.tape_budget_bytes ? p->opt.tape_budget_bytes : (size_t(1) << 30);
-  if (p->mode == KG_MODE_AUTO) p->mode = tape_bytes <= budget ? KG_MODE_TAPE : KG_MODE_RECOMPUTE;
+  size_t budget = p->opt.tape_budget_bytes ? p->opt.tape_budget_bytes : (size_t(1) << 30);
   p->tet_block = p->opt.block ? p->opt.block : 256;
   if (p->tet_block != 256) return fail(KG_ERR_UNSUPPORTED, "TETENERGY: block must be 256");
   p->tet_grid = tet_staged_grid(p);
   kg_status rc = ws_common(p, p->tet_grid, s);
   if (rc != KG_OK) return rc;
-  if (p->mode == KG_MODE_TAPE || p->strategy == KG_STRATEGY_CSR) {
-    if ((rc = ws_alloc(p, &p->tape, tape_bytes, "tape c_e")) != KG_OK) return rc;
-  }
   // FP64 arithmetic: float pairs when G is within the pair range (u is checked per call)
   if (p->dtype == KG_F32) {
     p->arith = KG_ARITH_NATIVE;
@@ -171,6 +167,19 @@ kg_status tet_setup(kg_problem* p, cudaStream_t s) {
       return fail(KG_ERR_UNSUPPORTED, "TETENERGY PAIR arithmetic: G has entries outside "
                                       "0 or [2^-60, 2^40) in magnitude");
     p->arith = in_range ? KG_ARITH_PAIR : KG_ARITH_NATIVE;
+  }
+  // Pair arithmetic: G split into float pairs once (same bytes) when it fits the
+  // budget; the kernels then stream that copy and skip 12 splits per element.
+  const size_t gprep_bytes = 12 * sizeof(double) * (size_t)p->m;
+  if (p->arith == KG_ARITH_PAIR && gprep_bytes <= budget) {
+    if ((rc = ws_alloc(p, &p->aprep, gprep_bytes, "prepared G (float pairs)")) != KG_OK) return rc;
+    if ((rc = pair_prepare(static_cast<const double*>(p->data1), p->aprep, 12 * p->m, s)) != KG_OK)
+      return rc;
+    budget -= gprep_bytes;
+  }
+  if (p->mode == KG_MODE_AUTO) p->mode = tape_bytes <= budget ? KG_MODE_TAPE : KG_MODE_RECOMPUTE;
+  if (p->mode == KG_MODE_TAPE || p->strategy == KG_STRATEGY_CSR) {
+    if ((rc = ws_alloc(p, &p->tape, tape_bytes, "tape c_e")) != KG_OK) return rc;
   }
   if ((rc = tet_staged_setup(p)) != KG_OK) return rc;
   const int64_t n4 = 4 * p->m;

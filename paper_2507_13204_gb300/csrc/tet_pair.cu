@@ -28,6 +28,7 @@
 #include <cstdlib>
 #include <mutex>
 #include <string>
+#include <type_traits>
 
 #include "kg_device.cuh"
 #include "kg_internal.h"
@@ -48,7 +49,7 @@ __host__ __device__ constexpr int ts_hash_slots() { return 2048; }
 template <typename T>
 struct TsArgs {
   const int4* conn;
-  const T* G;
+  const T* G;  // N_e x 12 values, or (PREP) N_e x 12 float pairs in the same bytes
   const T* u;
   int64_t ne;
   int nv;
@@ -64,7 +65,7 @@ struct TsArgs {
   LogConsts K;
 };
 
-template <typename T, bool PAIR, int MODE, bool SHARED>
+template <typename T, bool PAIR, int MODE, bool SHARED, bool PREP>
 __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr uint32_t kConnBytes = TS_THREADS * 16u;
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
         const int tb = (int)(i & 1) * kSlots;
         auto run = [&](const auto& sink) {
           if constexpr (PAIR) {
-            elem_pair<MODE>(c, reinterpret_cast<const double*>(Gs),
+            elem_pair<MODE, std::decay_t<decltype(sink)>, PREP>(c, reinterpret_cast<const double*>(Gs),
                             reinterpret_cast<const double*>(a.u), fb2, tab, a.K, facc_p, sink,
                             reinterpret_cast<double*>(a.tape) + e * 4, bad);
             if ((i & 31) == 31) acc_renorm(facc_p);
@@ -307,27 +308,28 @@ kg_status tet_staged_setup(kg_problem* p) {
   return KG_OK;
 }
 
-template <typename T, bool PAIR, int MODE>
-static cudaError_t launch_ts(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
-  if constexpr (MODE == TS_GRAD) {
-    if (p->strategy == KG_STRATEGY_SHARED) {
-      auto kern = tet_staged_kernel<T, PAIR, MODE, true>;
-      const size_t smem = ts_smem<T, PAIR, true>();
-      cudaError_t e =
-          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      if (e != cudaSuccess) return e;
-      static int occ = 0;
-      kern<<<ts_grid_for(p, kern, smem, occ), TS_THREADS, smem, s>>>(a);
-      return cudaGetLastError();
-    }
-  }
-  auto kern = tet_staged_kernel<T, PAIR, MODE, false>;
-  const size_t smem = ts_smem<T, PAIR, false>();
+template <typename T, bool PAIR, int MODE, bool SHARED, bool PREP>
+static cudaError_t launch_ts_k(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
+  auto kern = tet_staged_kernel<T, PAIR, MODE, SHARED, PREP>;
+  const size_t smem = ts_smem<T, PAIR, SHARED>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   static int occ = 0;
   kern<<<ts_grid_for(p, kern, smem, occ), TS_THREADS, smem, s>>>(a);
   return cudaGetLastError();
+}
+
+template <typename T, bool PAIR, int MODE>
+static cudaError_t launch_ts(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
+  const bool shared = MODE == TS_GRAD && p->strategy == KG_STRATEGY_SHARED;
+  if constexpr (PAIR) {
+    if (p->aprep) {
+      return shared ? launch_ts_k<T, PAIR, MODE, MODE == TS_GRAD, true>(p, a, s)
+                    : launch_ts_k<T, PAIR, MODE, false, true>(p, a, s);
+    }
+  }
+  return shared ? launch_ts_k<T, PAIR, MODE, MODE == TS_GRAD, false>(p, a, s)
+                : launch_ts_k<T, PAIR, MODE, false, false>(p, a, s);
 }
 
 template <typename T>
@@ -350,7 +352,7 @@ static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, v
                               const void* seed, cudaStream_t s) {
   TsArgs<T> a{};
   a.conn = static_cast<const int4*>(p->data0);
-  a.G = static_cast<const T*>(p->data1);
+  a.G = static_cast<const T*>(p->aprep ? p->aprep : p->data1);
   a.u = static_cast<const T*>(x);
   a.ne = p->m;
   a.nv = (int)p->n;

@@ -238,3 +238,27 @@ def test_strategy_defaults(api):
     p64 = api.TetEnergy(conn, torch.tensor(mesh.G, device="cuda"), mesh.nv)
     p32 = api.TetEnergy(conn, torch.tensor(mesh.G, dtype=torch.float32, device="cuda"), mesh.nv)
     assert p64.config[0] == "atomic" and p32.config[0] == "shared"
+
+
+def test_prepared_G_and_on_the_fly_split_agree(api):
+    # FP64 pair arithmetic keeps G split into float pairs when 96 N_e bytes fit the workspace
+    # budget; below it the kernels split G on every call.  Same split, same results (the CSR
+    # gather and the fixed-order value sum are bitwise reproducible).
+    mesh = W.tet_mesh(10, jitter_seed=3, perm_seed=6)
+    u = np.random.default_rng(8).uniform(-1, 1, mesh.nv)
+    f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
+    prep = _problem(api, mesh, torch.float64, strategy="csr")
+    fly = _problem(api, mesh, torch.float64, strategy="csr", tape_budget_bytes=96 * mesh.ne - 8)
+    assert prep.config[2] == fly.config[2] == "pair"
+    assert prep.workspace_bytes - fly.workspace_bytes == 96 * mesh.ne
+    ut = torch.tensor(u, device="cuda")
+    out = []
+    for p in (prep, fly):
+        f, g = p.grad(ut)
+        fe = p.eval(ut)
+        p.sync()
+        assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+        assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+        out.append((f.clone(), g.clone(), fe.clone()))
+    for a, b in zip(*out):
+        assert torch.equal(a, b)
