@@ -593,7 +593,7 @@ def main():
                     help="problem size override (dense n, tet cubes per axis, 1-D n) for small "
                          "profiling cases; the default is the full workload")
     ap.add_argument("--rows", type=int, default=0, help="dense: rows of A (default: square)")
-    ap.add_argument("--strategy", default="", choices=["", "atomic", "shared", "csr"],
+    ap.add_argument("--strategy", default="", choices=["", "atomic", "shared", "warp", "csr"],
                     help="tet: reverse-pass strategy (default: the library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -92,15 +92,19 @@ typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
  *             elements first combined per vertex in a shared-memory table, then
  *             one global atomic per distinct vertex (Sec. 5: shared memory for
  *             temporaries to reduce atomics).
- *   AUTO      FUSED for dense, ATOMIC for FP64 tets, SHARED for FP32 tets, the
- *             stencil transpose for 1-D. */
+ *   WARP      (tet) the forward schedule with the scatter-adds combined within
+ *             each warp: lanes whose element shares a vertex (in the same local
+ *             slot) add their values by shuffles and one lane issues the
+ *             atomic.
+ *   AUTO      FUSED for dense, WARP for tets, the stencil transpose for 1-D. */
 typedef enum {
   KG_STRATEGY_AUTO = 0,
   KG_STRATEGY_ATOMIC = 1,
   KG_STRATEGY_CSR = 2,
   KG_STRATEGY_TRANSPOSE = 3,
   KG_STRATEGY_FUSED = 4,
-  KG_STRATEGY_SHARED = 5
+  KG_STRATEGY_SHARED = 5,
+  KG_STRATEGY_WARP = 6
 } kg_strategy;
 
 /* Forward values for the reverse pass (Sec. 5, taping restriction).

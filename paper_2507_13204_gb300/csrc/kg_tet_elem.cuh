@@ -7,7 +7,8 @@
 // global memory; HashSink first combines the contributions of a tile of
 // elements per vertex in a shared-memory open-addressing table (Sec. 5:
 // shared memory for temporaries), which hash_flush then adds into gu with one
-// global atomic per distinct vertex.
+// global atomic per distinct vertex; CollectSink keeps them in registers for
+// warp_combine, which merges equal vertices across the lanes of a warp.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,11 +27,61 @@ __device__ __forceinline__ Acc shfl_xor_acc2(Acc a, int o) {
   return b;
 }
 
+// Sinks receive contribution k (0..3, the element's local vertex) for global
+// vertex v.  sink_pair gives a sink the float-pair value of the pair kernels;
+// by default it is converted to double first.
+__device__ __forceinline__ float shfl_v(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_v(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ Acc shfl_v(Acc v, int src) {
+  return Acc{__shfl_sync(0xffffffffu, v.s, src), __shfl_sync(0xffffffffu, v.l, src)};
+}
+
 template <typename T>
 struct AtomicSink {
   T* gu;
-  __device__ __forceinline__ void operator()(int v, T c) const { atomicAdd(gu + v, c); }
+  __device__ __forceinline__ void operator()(int, int v, T c) const { atomicAdd(gu + v, c); }
 };
+
+template <typename Sink>
+__device__ __forceinline__ void sink_pair(const Sink& gu, int k, int v, Pair c) {
+  gu(k, v, pair_to_double_fast(c));
+}
+
+// Keeps the element's four contributions in registers (k is a compile-time
+// index after unrolling) for the warp-level combine below.
+template <typename T>
+struct CollectSink {
+  T* vals;    // [4]
+  Pair* prs;  // [4], pair kernels
+  __device__ __forceinline__ void operator()(int k, int, T c) const { vals[k] = c; }
+};
+
+template <typename T>
+__device__ __forceinline__ void sink_pair(const CollectSink<T>& gu, int k, int, Pair c) {
+  gu.prs[k] = c;
+}
+
+// Warp-level combine of one contribution per lane: lanes whose key (vertex)
+// is equal form a group (match.any); every lane walks the group members above
+// it, adding their values (shuffles), so the lowest lane of each group ends
+// with the group total and adds it to gu with one atomic.  Inactive lanes take
+// part in the shuffles only.  All 32 lanes must call it together.
+template <typename V, typename AddF, typename FlushF>
+__device__ __forceinline__ void warp_combine(bool active, int key, V val, AddF add, FlushF flush) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, active ? key : -1);
+  unsigned rest = active ? peers & (0xFFFFFFFEu << lane) : 0u;
+  V acc = val;
+  while (__any_sync(0xffffffffu, rest != 0u)) {
+    const int src = rest ? __ffs(rest) - 1 : lane;
+    const V other = shfl_v(val, src);
+    if (rest) {
+      acc = add(acc, other);
+      rest &= rest - 1u;
+    }
+  }
+  if (active && (peers & ((1u << lane) - 1u)) == 0u) flush(key, acc);
+}
 
 // Per-tile table of (vertex, partial sum) in shared memory.  keys[] holds -1
 // for an empty slot.  Insertion probes linearly from a multiplicative hash;
@@ -43,7 +94,7 @@ struct HashSink {
   int* keys;
   T* vals;
   T* gu;
-  __device__ __forceinline__ void operator()(int v, T c) const {
+  __device__ __forceinline__ void operator()(int, int v, T c) const {
     static_assert((SLOTS & (SLOTS - 1)) == 0, "SLOTS must be a power of two");
     unsigned h = ((unsigned)v * 2654435761u) >> (32 - __builtin_ctz(SLOTS));
     for (int probe = 0; probe < SLOTS; ++probe) {
@@ -102,10 +153,10 @@ __device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ 
     const T c2 = G[2] * w0 + G[6] * w1 + G[10] * w2;
     const T c3 = G[3] * w0 + G[7] * w1 + G[11] * w2;
     if constexpr (MODE == TS_GRAD) {
-      gu(c.x, c0);
-      gu(c.y, c1);
-      gu(c.z, c2);
-      gu(c.w, c3);
+      gu(0, c.x, c0);
+      gu(1, c.y, c1);
+      gu(2, c.z, c2);
+      gu(3, c.w, c3);
     } else {
       tape_e[0] = c0;
       tape_e[1] = c1;
@@ -162,20 +213,23 @@ __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict
     Pair wg[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) wg[r] = pair_mul(w, g[r]);
-    double cd[4];
+    Pair cp[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       Acc a = acc_zero();
 #pragma unroll
       for (int r = 0; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, wg[r].h, wg[r].l);
-      cd[k] = pair_to_double_fast(acc_pair(a));
+      cp[k] = acc_pair(a);
     }
     if constexpr (MODE == TS_GRAD) {
-      gu(c.x, cd[0]);
-      gu(c.y, cd[1]);
-      gu(c.z, cd[2]);
-      gu(c.w, cd[3]);
+      sink_pair(gu, 0, c.x, cp[0]);
+      sink_pair(gu, 1, c.y, cp[1]);
+      sink_pair(gu, 2, c.z, cp[2]);
+      sink_pair(gu, 3, c.w, cp[3]);
     } else {
+      double cd[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cd[k] = pair_to_double_fast(cp[k]);
       reinterpret_cast<double2*>(tape_e)[0] = make_double2(cd[0], cd[1]);
       reinterpret_cast<double2*>(tape_e)[1] = make_double2(cd[2], cd[3]);
     }

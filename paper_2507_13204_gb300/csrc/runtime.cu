@@ -191,7 +191,7 @@ kg_status kg_create(kg_problem** out, int kind, const int64_t* sizes, int nsizes
   if (opt) o = *opt;
   if (o.dtype != KG_F64 && o.dtype != KG_F32)
     return fail(KG_ERR_INVALID_ARG, "kg_create: dtype must be KG_F64 or KG_F32");
-  if (o.strategy < KG_STRATEGY_AUTO || o.strategy > KG_STRATEGY_SHARED)
+  if (o.strategy < KG_STRATEGY_AUTO || o.strategy > KG_STRATEGY_WARP)
     return fail(KG_ERR_INVALID_ARG, "kg_create: bad strategy");
   if (o.mode < KG_MODE_AUTO || o.mode > KG_MODE_TAPE)
     return fail(KG_ERR_INVALID_ARG, "kg_create: bad mode");

@@ -18,23 +18,46 @@
 
 #include "kg_device.cuh"
 #include "kg_internal.h"
+#include "kg_tet_elem.cuh"
 
 namespace kg {
 
-// Reverse from the tape with the forward schedule: atomic scatter of fbar*c_e.
-template <typename T>
+// Reverse from the tape with the forward schedule: scatter of fbar*c_e, each
+// contribution an atomic (ATOMIC, SHARED, FP64 WARP) or combined within the
+// warp first (FP32 WARP, see warp_combine).  The loop is uniform per block so that every lane
+// of a warp reaches the warp-level combine.
+template <typename T, bool WARPC>
 __global__ void __launch_bounds__(256) tet_tape_scatter_kernel(const int4* __restrict__ conn,
                                                                const T* __restrict__ tape,
                                                                int64_t ne, const T* seed, T* gu) {
   const T fb = load_seed(seed);
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ne; e += stride) {
-    const int4 c = __ldcs(conn + e);
-    const T* t = tape + e * 4;
-    atomicAdd(gu + c.x, fb * t[0]);
-    atomicAdd(gu + c.y, fb * t[1]);
-    atomicAdd(gu + c.z, fb * t[2]);
-    atomicAdd(gu + c.w, fb * t[3]);
+  for (int64_t e0 = (int64_t)blockIdx.x * blockDim.x; e0 < ne; e0 += stride) {
+    const int64_t e = e0 + threadIdx.x;
+    const bool act = e < ne;
+    int4 c = make_int4(-1, -1, -1, -1);
+    T t[4] = {T(0), T(0), T(0), T(0)};
+    if (act) {
+      c = __ldcs(conn + e);
+      if constexpr (sizeof(T) == 8) {
+        const double2 a = __ldcs(reinterpret_cast<const double2*>(tape) + 2 * e);
+        const double2 b = __ldcs(reinterpret_cast<const double2*>(tape) + 2 * e + 1);
+        t[0] = a.x, t[1] = a.y, t[2] = b.x, t[3] = b.y;
+      } else {
+        const float4 a = __ldcs(reinterpret_cast<const float4*>(tape) + e);
+        t[0] = a.x, t[1] = a.y, t[2] = a.z, t[3] = a.w;
+      }
+    }
+    const int key[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if constexpr (WARPC) {
+        warp_combine(act, key[k], fb * t[k], [](T x, T y) { return x + y; },
+                     [&](int v, T tot) { atomicAdd(gu + v, tot); });
+      } else if (act) {
+        atomicAdd(gu + key[k], fb * t[k]);
+      }
+    }
   }
 }
 
@@ -144,11 +167,10 @@ static int grid_for(int64_t work, int block, int per_sm) {
 kg_status tet_setup(kg_problem* p, cudaStream_t s) {
   if (p->m * 4 >= (int64_t(1) << 31))
     return fail(KG_ERR_INVALID_ARG, "TETENERGY: 4 * N_e must be < 2^31");
-  if (p->strategy == KG_STRATEGY_AUTO)
-    p->strategy = p->dtype == KG_F32 ? KG_STRATEGY_SHARED : KG_STRATEGY_ATOMIC;
+  if (p->strategy == KG_STRATEGY_AUTO) p->strategy = KG_STRATEGY_WARP;
   if (p->strategy != KG_STRATEGY_ATOMIC && p->strategy != KG_STRATEGY_CSR &&
-      p->strategy != KG_STRATEGY_SHARED)
-    return fail(KG_ERR_UNSUPPORTED, "TETENERGY: strategy must be ATOMIC, SHARED or CSR");
+      p->strategy != KG_STRATEGY_SHARED && p->strategy != KG_STRATEGY_WARP)
+    return fail(KG_ERR_UNSUPPORTED, "TETENERGY: strategy must be ATOMIC, SHARED, WARP or CSR");
   const size_t tape_bytes = p->esize * 4 * (size_t)p->m;
   size_t budget = p->opt.tape_budget_bytes ? p->opt.tape_budget_bytes : (size_t(1) << 30);
   p->tet_block = p->opt.block ? p->opt.block : 256;
@@ -245,9 +267,13 @@ static kg_status tet_scatter_t(kg_problem* p, void* gx, const void* seed, int ac
       count_launch();
     }
     prof_begin(s, "tet_tape_scatter_kernel");
-    tet_tape_scatter_kernel<T><<<p->tet_grid, 256, 0, s>>>(
-        static_cast<const int4*>(p->data0), static_cast<const T*>(p->tape), p->m,
-        static_cast<const T*>(seed), static_cast<T*>(gx));
+    // FP64 tape values would be combined with FP64 adds, which cost more here than the
+    // atomics they save (measured): the warp combine is used for FP32 tapes only
+    auto kern = p->strategy == KG_STRATEGY_WARP && sizeof(T) == 4 ? tet_tape_scatter_kernel<T, true>
+                                                                  : tet_tape_scatter_kernel<T, false>;
+    kern<<<p->tet_grid, 256, 0, s>>>(static_cast<const int4*>(p->data0),
+                                     static_cast<const T*>(p->tape), p->m,
+                                     static_cast<const T*>(seed), static_cast<T*>(gx));
     prof_end(s);
     count_launch();
   }

@@ -17,6 +17,13 @@
 // tile of 256 tets of the Kuhn grid touches ~180 distinct vertices for its
 // 1024 contributions, so global atomics drop ~5x.
 //
+// KG_STRATEGY_WARP: the four contributions of each lane stay in registers;
+// per local vertex slot k, lanes of a warp holding the same global vertex
+// (match.any) add their values by shuffles (float pairs for FP64 data) and
+// the lowest lane of each group issues one atomic.  No shared memory and no
+// CTA barrier; on the Kuhn grid (six consecutive tets share the cube's
+// diagonal ends in slots 0 and 3) global atomics drop ~3x.
+//
 // Arithmetic: FP32 for FP32 problems; for FP64 problems either native FP64
 // or float pairs (kg_pair.cuh) with the results converted back to double for
 // the atomics / tape (KG_ARITH_PAIR: GB300's FP64 units are ~60x slower than
@@ -65,8 +72,13 @@ struct TsArgs {
   LogConsts K;
 };
 
-template <typename T, bool PAIR, int MODE, bool SHARED, bool PREP>
+// Scatter of the reverse pass (GRAD mode).
+enum { SC_ATOMIC = 0, SC_SHARED = 1, SC_WARP = 2 };
+
+template <typename T, bool PAIR, int MODE, int SCAT, bool PREP>
 __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
+  constexpr bool SHARED = SCAT == SC_SHARED;
+  constexpr bool WARPC = SCAT == SC_WARP && MODE == TS_GRAD;
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr uint32_t kConnBytes = TS_THREADS * 16u;
   constexpr uint32_t kGBytes = TS_THREADS * 12u * sizeof(T);
@@ -144,6 +156,10 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
       ok = false;
     }
     const int64_t e = (blockIdx.x + i * (int64_t)gridDim.x) * TS_THREADS + tid;
+    T wv[4];        // WARPC: this lane's contributions and their vertices
+    Pair wp[4];
+    int4 wc = make_int4(-1, -1, -1, -1);
+    bool wact = false;
     if (ok && e < a.ne) {
       const unsigned char* st = smem + s * kStage;
       const int4 c = reinterpret_cast<const int4*>(st)[tid];
@@ -166,8 +182,32 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
             elem_native<T, MODE>(c, Gs, a.u, fb, facc_n, sink, a.tape + e * 4);
           }
         };
-        if constexpr (SHARED) run(HashSink<T, kSlots>{hkeys + tb, hvals + tb, a.gu});
-        else run(AtomicSink<T>{a.gu});
+        if constexpr (SHARED) {
+          run(HashSink<T, kSlots>{hkeys + tb, hvals + tb, a.gu});
+        } else if constexpr (WARPC) {
+          run(CollectSink<T>{wv, wp});
+          wc = c;
+          wact = true;
+        } else {
+          run(AtomicSink<T>{a.gu});
+        }
+      }
+    }
+    if constexpr (WARPC) {  // every lane of the warp, active or not
+      const int key[4] = {wc.x, wc.y, wc.z, wc.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if constexpr (PAIR) {
+          warp_combine(wact, key[k], Acc{wp[k].h, wp[k].l},
+                       [](Acc x, Acc y) { return acc_add(x, y); },
+                       [&](int v, Acc tot) {
+                         atomicAdd(reinterpret_cast<double*>(a.gu) + v,
+                                   pair_to_double_fast(acc_pair(tot)));
+                       });
+        } else {
+          warp_combine(wact, key[k], wv[k], [](T x, T y) { return x + y; },
+                       [&](int v, T tot) { atomicAdd(a.gu + v, tot); });
+        }
       }
     }
     if constexpr (SHARED) {  // the tile's insertions are complete: add the table into gu
@@ -308,10 +348,10 @@ kg_status tet_staged_setup(kg_problem* p) {
   return KG_OK;
 }
 
-template <typename T, bool PAIR, int MODE, bool SHARED, bool PREP>
+template <typename T, bool PAIR, int MODE, int SCAT, bool PREP>
 static cudaError_t launch_ts_k(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
-  auto kern = tet_staged_kernel<T, PAIR, MODE, SHARED, PREP>;
-  const size_t smem = ts_smem<T, PAIR, SHARED>();
+  auto kern = tet_staged_kernel<T, PAIR, MODE, SCAT, PREP>;
+  const size_t smem = ts_smem<T, PAIR, SCAT == SC_SHARED>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   static int occ = 0;
@@ -319,17 +359,21 @@ static cudaError_t launch_ts_k(const kg_problem* p, const TsArgs<T>& a, cudaStre
   return cudaGetLastError();
 }
 
+template <typename T, bool PAIR, int MODE, bool PREP>
+static cudaError_t launch_ts_p(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
+  if constexpr (MODE == TS_GRAD) {
+    if (p->strategy == KG_STRATEGY_SHARED) return launch_ts_k<T, PAIR, MODE, SC_SHARED, PREP>(p, a, s);
+    if (p->strategy == KG_STRATEGY_WARP) return launch_ts_k<T, PAIR, MODE, SC_WARP, PREP>(p, a, s);
+  }
+  return launch_ts_k<T, PAIR, MODE, SC_ATOMIC, PREP>(p, a, s);
+}
+
 template <typename T, bool PAIR, int MODE>
 static cudaError_t launch_ts(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
-  const bool shared = MODE == TS_GRAD && p->strategy == KG_STRATEGY_SHARED;
   if constexpr (PAIR) {
-    if (p->aprep) {
-      return shared ? launch_ts_k<T, PAIR, MODE, MODE == TS_GRAD, true>(p, a, s)
-                    : launch_ts_k<T, PAIR, MODE, false, true>(p, a, s);
-    }
+    if (p->aprep) return launch_ts_p<T, PAIR, MODE, true>(p, a, s);
   }
-  return shared ? launch_ts_k<T, PAIR, MODE, MODE == TS_GRAD, false>(p, a, s)
-                : launch_ts_k<T, PAIR, MODE, false, false>(p, a, s);
+  return launch_ts_p<T, PAIR, MODE, false>(p, a, s);
 }
 
 template <typename T>

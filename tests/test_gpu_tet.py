@@ -1,6 +1,6 @@
 """GPU parity: tet-mesh energy value and gradient (atomic scatter, shared-memory
-aggregated scatter and CSR gather; recompute and tape) through the C ABI vs the
-CPU oracle."""
+and warp aggregated scatters, CSR gather; recompute and tape) through the C ABI
+vs the CPU oracle."""
 import numpy as np
 import pytest
 import torch
@@ -30,7 +30,7 @@ MESHES = [(1, None), (3, 2), (7, None), (12, 2), (25, 2)]
 
 
 @pytest.mark.parametrize("a,jit", MESHES)
-@pytest.mark.parametrize("strategy", ["atomic", "shared", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
 def test_f64_grad_matches_oracle(api, a, jit, strategy):
     mesh = W.tet_mesh(a, jitter_seed=jit, perm_seed=a)
     u = np.random.default_rng(a).uniform(-1, 1, mesh.nv)
@@ -45,7 +45,7 @@ def test_f64_grad_matches_oracle(api, a, jit, strategy):
     assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
 
 
-@pytest.mark.parametrize("strategy", ["atomic", "shared", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
 def test_f32_matches_oracle_on_rounded_inputs(api, strategy):
     mesh = W.tet_mesh(20, jitter_seed=2, perm_seed=3)
     u = np.random.default_rng(5).uniform(-1, 1, mesh.nv)
@@ -60,7 +60,7 @@ def test_f32_matches_oracle_on_rounded_inputs(api, strategy):
     assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f32"]
 
 
-@pytest.mark.parametrize("strategy", ["atomic", "shared", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
 def test_tape_mode_seed_and_accumulate(api, strategy):
     mesh = W.tet_mesh(9, jitter_seed=2, perm_seed=4)
     u = np.random.default_rng(6).uniform(-1, 1, mesh.nv)
@@ -120,7 +120,7 @@ def test_full_size_100_cubed_f64(api):
     mesh, u = W.tet_inputs(100)
     f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
     ut = torch.tensor(u, device="cuda")
-    for strategy in ("atomic", "shared", "csr"):
+    for strategy in ("atomic", "shared", "warp", "csr"):
         p = _problem(api, mesh, torch.float64, strategy=strategy)
         f, g = p.grad(ut)
         fe = p.eval(ut)
@@ -156,7 +156,7 @@ def test_checked_kernels_flag_connectivity_changed_after_create(api):
 
 
 @pytest.mark.parametrize("arith", ["pair", "native"])
-@pytest.mark.parametrize("strategy", ["atomic", "shared", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
 def test_pair_and_native_match_oracle_jittered(api, arith, strategy):
     mesh = W.tet_mesh(18, jitter_seed=2, perm_seed=5)
     u = np.random.default_rng(21).uniform(-1, 1, mesh.nv)
@@ -179,7 +179,7 @@ def test_pair_default_and_range_rules(api):
     from paper_2507_13204_gb300 import _lib as L
     mesh = W.tet_mesh(5, jitter_seed=2)
     p = _problem(api, mesh, torch.float64)
-    assert p.config == ("atomic", "tape", "pair")
+    assert p.config == ("warp", "tape", "pair")
     u = np.random.default_rng(1).uniform(-1, 1, mesh.nv)
     u[3] = 1e200  # outside the pair range: reported, not silently wrong
     p.grad(torch.tensor(u, device="cuda"))
@@ -203,7 +203,7 @@ def test_ragged_tiles_and_tiny_meshes(api):
         u = np.random.default_rng(a * b * c).uniform(-1, 1, mesh.nv)
         f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
         for arith in ("pair", "native"):
-            for strategy in ("atomic", "shared"):
+            for strategy in ("atomic", "shared", "warp"):
                 p = _problem(api, mesh, torch.float64, arith=arith, strategy=strategy)
                 f, g = p.grad(torch.tensor(u, device="cuda"))
                 p.sync()
@@ -211,10 +211,12 @@ def test_ragged_tiles_and_tiny_meshes(api):
                 assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
 
 
+@pytest.mark.parametrize("strategy", ["shared", "warp"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
-def test_shared_aggregation_with_scattered_element_order(api, dtype):
+def test_aggregation_with_scattered_element_order(api, dtype, strategy):
     # elements in random order: a 256-tet tile then touches ~1000 distinct vertices, close to
-    # the worst case for the shared-memory table (long probe chains, nearly no combining)
+    # the worst case for the shared-memory table (long probe chains, nearly no combining),
+    # and lanes of a warp rarely share a vertex
     mesh = W.tet_mesh(14, jitter_seed=2, perm_seed=8)
     order = np.random.default_rng(12).permutation(mesh.ne)
     conn, G = np.ascontiguousarray(mesh.conn[order]), np.ascontiguousarray(mesh.G[order])
@@ -223,8 +225,8 @@ def test_shared_aggregation_with_scattered_element_order(api, dtype):
         G, u = f32_round(G), f32_round(u)
     f_ref, g_ref = O.tet_grad(conn, G, u)
     p = api.TetEnergy(torch.tensor(conn, device="cuda"), torch.tensor(G, dtype=dtype, device="cuda"),
-                      mesh.nv, strategy="shared")
-    assert p.config[0] == "shared"
+                      mesh.nv, strategy=strategy)
+    assert p.config[0] == strategy
     f, g = p.grad(torch.tensor(u, dtype=dtype, device="cuda"))
     p.sync()
     tol = TOL["f64"] if dtype == torch.float64 else TOL["f32"]
@@ -237,7 +239,7 @@ def test_strategy_defaults(api):
     conn = torch.tensor(mesh.conn, device="cuda")
     p64 = api.TetEnergy(conn, torch.tensor(mesh.G, device="cuda"), mesh.nv)
     p32 = api.TetEnergy(conn, torch.tensor(mesh.G, dtype=torch.float32, device="cuda"), mesh.nv)
-    assert p64.config[0] == "atomic" and p32.config[0] == "shared"
+    assert p64.config[0] == "warp" and p32.config[0] == "warp"
 
 
 def test_prepared_G_and_on_the_fly_split_agree(api):
@@ -262,3 +264,26 @@ def test_prepared_G_and_on_the_fly_split_agree(api):
         out.append((f.clone(), g.clone(), fe.clone()))
     for a, b in zip(*out):
         assert torch.equal(a, b)
+
+
+def test_warp_combine_on_a_mesh_where_every_tet_shares_one_vertex(api):
+    # a fan of tets around vertex 0: all 32 lanes of every warp hold vertex 0 in slot 0, the
+    # largest possible group (31 shuffle rounds), and the other slots are all distinct
+    rng = np.random.default_rng(21)
+    ne = 1000
+    conn = np.zeros((ne, 4), dtype=np.int32)
+    conn[:, 1:] = 1 + np.arange(3 * ne, dtype=np.int32).reshape(ne, 3)
+    G = rng.uniform(-1, 1, (ne, 12))
+    u = rng.uniform(-1, 1, 3 * ne + 1)
+    f_ref, g_ref = O.tet_grad(conn, G, u)
+    for dtype in (torch.float64, torch.float32):
+        Gd, ud = (G, u) if dtype == torch.float64 else (f32_round(G), f32_round(u))
+        if dtype == torch.float32:
+            f_ref, g_ref = O.tet_grad(conn, Gd, ud)
+        p = api.TetEnergy(torch.tensor(conn, device="cuda"), torch.tensor(Gd, dtype=dtype, device="cuda"),
+                          3 * ne + 1, strategy="warp")
+        f, g = p.grad(torch.tensor(ud, dtype=dtype, device="cuda"))
+        p.sync()
+        tol = TOL["f64"] if dtype == torch.float64 else TOL["f32"]
+        assert rel_scalar(f.item(), f_ref) <= tol
+        assert rel_l2(g.cpu().numpy(), g_ref) <= tol
