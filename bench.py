@@ -345,8 +345,8 @@ class BatchedWL(Workload):
     compared with the per-instance launch loop."""
     unit = "grads/s"
 
-    def __init__(self, ndense=4096, ntet=512, arith="auto"):
-        self.ndense, self.ntet, self.arith = ndense, ntet, arith
+    def __init__(self, ndense=4096, ntet=512, arith="auto", strategy="auto"):
+        self.ndense, self.ntet, self.arith, self.strategy = ndense, ntet, arith, strategy
         self.es = 8
 
     def setup(self, dev):
@@ -383,7 +383,7 @@ class BatchedWL(Workload):
             self.xs[i].copy_(x)
         for j, (mesh, u, _, _) in enumerate(self.tets):
             self.xs[self.ndense + j].copy_(torch.tensor(u, device=dev))
-        self.batch = api.Batch(probs, arith=self.arith)
+        self.batch = api.Batch(probs, arith=self.arith, strategy=self.strategy)
         self.x_pin = self.xbuf.cpu().pin_memory()
         self.g_pin = torch.empty_like(self.gbuf, device="cpu").pin_memory()
         self.f_pin = torch.empty_like(self.fbuf, device="cpu").pin_memory()
@@ -543,7 +543,8 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
     if name == "autograd32":
         return AutogradWL(size or 100, "f32")
     if name == "batched":
-        return BatchedWL(size or 4096, max(1, (size or 4096) // 8), arith=arith)
+        return BatchedWL(size or 4096, max(1, (size or 4096) // 8), arith=arith,
+                         strategy=strategy or "auto")
     if name == "dense":
         return DenseWL(size or 10000, "f64", arith=arith, m=rows or None)
     if name == "dense32":
@@ -594,7 +595,8 @@ def main():
                          "profiling cases; the default is the full workload")
     ap.add_argument("--rows", type=int, default=0, help="dense: rows of A (default: square)")
     ap.add_argument("--strategy", default="", choices=["", "atomic", "shared", "warp", "csr"],
-                    help="tet: reverse-pass strategy (default: the library's choice)")
+                    help="tet, batched: reverse-pass scatter strategy (default: the library's "
+                         "choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -205,6 +205,9 @@ kg_status kg_grad_host(kg_problem *p, const void *x_host, void *f_host, void *gx
  * host synchronisation points).  kg_batch_create autotunes the tile and team
  * sizes (cached in $KG_TUNE_CACHE, default ~/.cache/kg_tune.json, keyed by GPU
  * name, kind and size bucket), builds the work table and synchronises `s`.
+ * opt->strategy picks the tet scatter: AUTO or ATOMIC (one atomic per
+ * contribution) or WARP (warp-combined atomics, see KG_STRATEGY_WARP); others
+ * are KG_ERR_UNSUPPORTED.
  * The problems are borrowed and must outlive the batch. */
 kg_status kg_batch_create(kg_batch **out, kg_problem *const *probs, int count,
                           const kg_options *opt, kg_stream s);

@@ -151,9 +151,10 @@ class Laplace1D(Problem):
 class Batch:
     """Many problems differentiated by one persistent launch (graph-replayed)."""
 
-    def __init__(self, problems, arith="auto", stream=None):
+    def __init__(self, problems, arith="auto", strategy="auto", stream=None):
         self.problems = list(problems)
-        opt = L.options(dtype=_DT[self.problems[0].dtype], arith=ARITHS[arith])
+        opt = L.options(dtype=_DT[self.problems[0].dtype], arith=ARITHS[arith],
+                        strategy=STRATEGIES[strategy])
         self.handle = L.kg_batch_create([p.handle for p in self.problems], opt, stream)
 
     @property

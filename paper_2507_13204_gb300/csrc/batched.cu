@@ -11,7 +11,7 @@
 //   dense tile:  rows [r0, r0 + R): y_i by a row team (a warp for n <= 256,
 //                the CTA otherwise), ybar_i = 2 y_i, private xbar partial of
 //                the tile written to the instance's partial buffer;
-//   tet tile:    elements [e0, e0 + T): f_e and the atomic scatter of c_e
+//   tet tile:    elements [e0, e0 + T): f_e and the scatter of c_e (warp-combined atomics)
 //                into gu (zeroed by a small kernel earlier in the graph).
 // The CTA that finishes an instance's last tile (a per-instance arrival
 // counter; nobody waits) sums the instance's partials in tile order into gx
@@ -290,7 +290,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
 }
 
 // Elements [w.start, w.start + w.count) of a tet instance; returns the tile's f.
-template <typename T, bool PAIR>
+template <typename T, bool PAIR, bool WARPC>
 __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, const LogConsts& K,
                            double* red, bool& bad) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -302,15 +302,50 @@ __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, co
   T fn = T(0);
   const int64_t e1 = w.start + w.count;
   int cnt = 0;
-  for (int64_t e = w.start + tid; e < e1; e += BT, ++cnt) {
-    const int4 c = __ldcs(conn + e);
-    if constexpr (PAIR) {
-      elem_pair<TS_GRAD>(c, reinterpret_cast<const double*>(G) + e * 12,
-                         reinterpret_cast<const double*>(u), Pair{2.0f, 0.0f}, tab, K, fp,
-                         AtomicSink<double>{reinterpret_cast<double*>(gu)}, nullptr, bad);
-      if ((cnt & 31) == 31) acc_renorm(fp);
-    } else {
-      elem_native<T, TS_GRAD>(c, G + e * 12, u, T(1), fn, AtomicSink<T>{gu}, nullptr);
+  if constexpr (!WARPC) {  // one atomic per contribution
+    for (int64_t e = w.start + tid; e < e1; e += BT, ++cnt) {
+      const int4 c = __ldcs(conn + e);
+      if constexpr (PAIR) {
+        elem_pair<TS_GRAD>(c, reinterpret_cast<const double*>(G) + e * 12,
+                           reinterpret_cast<const double*>(u), Pair{2.0f, 0.0f}, tab, K, fp,
+                           AtomicSink<double>{reinterpret_cast<double*>(gu)}, nullptr, bad);
+        if ((cnt & 31) == 31) acc_renorm(fp);
+      } else {
+        elem_native<T, TS_GRAD>(c, G + e * 12, u, T(1), fn, AtomicSink<T>{gu}, nullptr);
+      }
+    }
+  }
+  // WARPC: block-uniform loop, so that every lane reaches the warp-level combine
+  for (int64_t e0 = w.start; WARPC && e0 < e1; e0 += BT, ++cnt) {
+    const int64_t e = e0 + tid;
+    const bool act = e < e1;
+    T cv[4];
+    Pair cpr[4];
+    int4 c = make_int4(-1, -1, -1, -1);
+    if (act) {
+      c = __ldcs(conn + e);
+      if constexpr (PAIR) {
+        elem_pair<TS_GRAD>(c, reinterpret_cast<const double*>(G) + e * 12,
+                           reinterpret_cast<const double*>(u), Pair{2.0f, 0.0f}, tab, K, fp,
+                           CollectSink<T>{cv, cpr}, nullptr, bad);
+        if ((cnt & 31) == 31) acc_renorm(fp);
+      } else {
+        elem_native<T, TS_GRAD>(c, G + e * 12, u, T(1), fn, CollectSink<T>{cv, cpr}, nullptr);
+      }
+    }
+    const int key[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      if constexpr (PAIR) {
+        warp_combine(act, key[k], Acc{cpr[k].h, cpr[k].l},
+                     [](Acc x, Acc y) { return acc_add(x, y); },
+                     [&](int v, Acc tot) {
+                       atomicAdd(reinterpret_cast<double*>(gu) + v, pair_to_double_fast(acc_pair(tot)));
+                     });
+      } else {
+        warp_combine(act, key[k], cv[k], [](T x, T y) { return x + y; },
+                     [&](int v, T tot) { atomicAdd(gu + v, tot); });
+      }
     }
   }
   __syncthreads();
@@ -362,7 +397,7 @@ __device__ void finalize(const BInst& I, double* red) {
   }
 }
 
-template <typename T, bool PAIR>
+template <typename T, bool PAIR, bool WARPC>
 __global__ void __launch_bounds__(BT) batched_kernel(BArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   float4* tab = reinterpret_cast<float4*>(smem);
@@ -404,7 +439,7 @@ __global__ void __launch_bounds__(BT) batched_kernel(BArgs a) {
         default: ft = dense_tile<T, PAIR, BT>(I, w, wsp, red, bad); break;
       }
     } else {
-      ft = tet_tile<T, PAIR>(I, w, tab, a.K, red, bad);
+      ft = tet_tile<T, PAIR, WARPC>(I, w, tab, a.K, red, bad);
     }
     if (tid == 0) I.fpart[w.tile] = ft;
     __threadfence();
@@ -627,16 +662,26 @@ int batched_grid(bool pair) {
   const size_t smem = batched_smem(pair);
   cudaError_t e;
   if (pair)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, true>, BT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, true, true>, BT, smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, false>, BT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, false, true>, BT, smem);
   if (e != cudaSuccess || per < 1) per = 2;
   return num_sms() * std::min(per, 4);
 }
 
 // Launches the zero kernel (tet gradients) and the persistent kernel on s.
-kg_status launch_plan(const DevPlan& D, int dtype, bool pair, unsigned* err, cudaStream_t s,
-                      int grid) {
+template <bool WARPC>
+static void launch_batched(int dtype, bool pair, int grid, size_t smem, cudaStream_t s, const BArgs& a) {
+  if (dtype == KG_F64) {
+    if (pair) batched_kernel<double, true, WARPC><<<grid, BT, smem, s>>>(a);
+    else batched_kernel<double, false, WARPC><<<grid, BT, smem, s>>>(a);
+  } else {
+    batched_kernel<float, false, WARPC><<<grid, BT, smem, s>>>(a);
+  }
+}
+
+kg_status launch_plan(const DevPlan& D, int dtype, bool pair, bool warp, unsigned* err,
+                      cudaStream_t s, int grid) {
   cudaError_t e = cudaSuccess;
   if (D.ntet > 0) {
     const int zg = std::min(D.ntet, num_sms() * 4);
@@ -656,12 +701,8 @@ kg_status launch_plan(const DevPlan& D, int dtype, bool pair, unsigned* err, cud
     if (rc != KG_OK) return rc;
   }
   const size_t smem = batched_smem(pair);
-  if (dtype == KG_F64) {
-    if (pair) batched_kernel<double, true><<<grid, BT, smem, s>>>(a);
-    else batched_kernel<double, false><<<grid, BT, smem, s>>>(a);
-  } else {
-    batched_kernel<float, false><<<grid, BT, smem, s>>>(a);
-  }
+  if (warp) launch_batched<true>(dtype, pair, grid, smem, s, a);
+  else launch_batched<false>(dtype, pair, grid, smem, s, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batched kernel");
   return KG_OK;
 }
@@ -672,6 +713,7 @@ struct kg_batch {
   std::vector<kg_problem*> probs;
   int dtype = KG_F64;
   bool pair = false;
+  bool warp = false;  // tet scatter: warp-combined atomics (false: one atomic per contribution)
   size_t es = 8;
   Plan plan;
   DevPlan dev;
@@ -722,7 +764,7 @@ kg_status time_plan(kg_batch* b, const std::vector<int>& ids, const Tuning& tu, 
     float best = 1e30f;
     for (int r = 0; rc == KG_OK && r < 4; ++r) {
       cudaEventRecord(e0, s);
-      rc = launch_plan(D, b->dtype, b->pair, b->err, s, b->grid);
+      rc = launch_plan(D, b->dtype, b->pair, b->warp, b->err, s, b->grid);
       cudaEventRecord(e1, s);
       if (rc == KG_OK && (e = cudaEventSynchronize(e1)) != cudaSuccess) rc = cuda_fail(e, "autotune");
       float t = 0.f;
@@ -826,7 +868,12 @@ kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count,
   b->dtype = b->probs[0] ? b->probs[0]->dtype : KG_F64;
   b->es = b->dtype == KG_F64 ? 8 : 4;
   kg_status rc = KG_OK;
+  const int strat = opt ? opt->strategy : KG_STRATEGY_AUTO;
+  if (strat != KG_STRATEGY_AUTO && strat != KG_STRATEGY_WARP && strat != KG_STRATEGY_ATOMIC)
+    rc = fail(KG_ERR_UNSUPPORTED, "kg_batch_create: strategy must be AUTO, WARP or ATOMIC");
+  b->warp = strat == KG_STRATEGY_WARP;  // AUTO: plain atomics (measured ~3% faster here)
   for (kg_problem* p : b->probs) {
+    if (rc != KG_OK) break;
     if (!p) rc = fail(KG_ERR_INVALID_ARG, "kg_batch_create: NULL problem");
     else if (p->dtype != b->dtype) rc = fail(KG_ERR_INVALID_ARG, "kg_batch_create: mixed dtypes");
     else if (p->kind == KG_QUADFORM && p->n > B_MAXN)
@@ -875,9 +922,12 @@ kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count,
     rc = devplan_alloc(b->dev, b->plan, s);
   }
   if (rc == KG_OK) {
-    cudaError_t e = cudaFuncSetAttribute(batched_kernel<double, true>,
+    cudaError_t e = cudaFuncSetAttribute(batched_kernel<double, true, true>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)batched_smem(true));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(batched_kernel<double, true, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batched_smem(true));
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = cuda_fail(e, "kg_batch_create");
   }
@@ -929,7 +979,7 @@ kg_status kg_grad_batched(kg_batch* b, const void* const* x, void* const* f, voi
       return cuda_fail(e, "kg_grad_batched: capture stream");
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-      rc = launch_plan(b->dev, b->dtype, b->pair, b->err, cs, b->grid);
+      rc = launch_plan(b->dev, b->dtype, b->pair, b->warp, b->err, cs, b->grid);
       cudaError_t e2 = cudaStreamEndCapture(cs, &b->graph);
       if (rc == KG_OK && e2 != cudaSuccess) rc = cuda_fail(e2, "kg_grad_batched: end capture");
     } else {

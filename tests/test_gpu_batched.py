@@ -55,11 +55,12 @@ DENSE = [32, 33, 64, 100, 255, 256, 257, 511, 1000, 1024, 1500, 2047, 2048]
 BOXES = [(1, 1, 1), (3, 3, 2), (5, 5, 7), (10, 10, 12)]
 
 
+@pytest.mark.parametrize("strategy", ["auto", "warp"])
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_batched_matches_oracle_per_instance(api, dtype, tmp_path, monkeypatch):
+def test_batched_matches_oracle_per_instance(api, dtype, strategy, tmp_path, monkeypatch):
     monkeypatch.setenv("KG_TUNE_CACHE", str(tmp_path / "tune.json"))
     probs, host, xs, fs, gxs = _make(api, dtype, DENSE, BOXES)
-    batch = api.Batch(probs)
+    batch = api.Batch(probs, strategy=strategy)
     batch.grad(xs, fs, gxs)
     batch.sync()
     tol = TOL[dtype]
