@@ -136,9 +136,20 @@ template <typename T, int MODE, typename Sink>
 __device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ Gs,
                                             const T* __restrict__ u, T fb, T& facc, const Sink& gu,
                                             T* tape_e) {
-  T G[12];
+  T G[12];  // Gs is 16-byte aligned (48 or 96 bytes per element): vector loads
+  if constexpr (sizeof(T) == 4) {
 #pragma unroll
-  for (int i = 0; i < 12; ++i) G[i] = Gs[i];
+    for (int i = 0; i < 12; i += 4) {
+      const float4 q = *reinterpret_cast<const float4*>(Gs + i);
+      G[i] = q.x, G[i + 1] = q.y, G[i + 2] = q.z, G[i + 3] = q.w;
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 12; i += 2) {
+      const double2 q = *reinterpret_cast<const double2*>(Gs + i);
+      G[i] = q.x, G[i + 1] = q.y;
+    }
+  }
   const T u0 = __ldg(u + c.x), u1 = __ldg(u + c.y), u2 = __ldg(u + c.z), u3 = __ldg(u + c.w);
   const T g0 = G[0] * u0 + G[1] * u1 + G[2] * u2 + G[3] * u3;
   const T g1 = G[4] * u0 + G[5] * u1 + G[6] * u2 + G[7] * u3;

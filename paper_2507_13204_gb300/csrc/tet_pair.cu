@@ -2,7 +2,7 @@
 //
 // Each CTA walks tiles of 256 elements (tile = blockIdx.x, + gridDim.x, ...).
 // Thread 0 streams each tile's connectivity (int4 per element) and G_e
-// (12 values per element) into a two-stage shared-memory ring with TMA bulk
+// (12 values per element) into a shared-memory ring (3 stages FP32, 2 FP64) with TMA bulk
 // copies (cp.async.bulk, mbarrier transaction counts); warps release a stage
 // through an "empty" mbarrier and thread 0 refills it.  Thread i of the CTA
 // handles element i of the tile: gathers u_e (4 reads through the index map,
@@ -46,7 +46,9 @@ namespace kg {
 
 constexpr int TS_THREADS = 256;  // threads per CTA == elements per tile
 constexpr int TS_WARPS = TS_THREADS / 32;
-constexpr int TS_STAGES = 2;
+// Shared-memory ring depth: 3 stages for the FP32 forward (16 KB each), else 2.
+template <typename T, int MODE>
+__host__ __device__ constexpr int ts_stages() { return sizeof(T) == 4 && MODE == TS_EVAL ? 3 : 2; }
 
 // Slots of one shared-memory aggregation table (power of two, > 4 x TS_THREADS).
 template <typename T>
@@ -79,6 +81,7 @@ template <typename T, bool PAIR, int MODE, int SCAT, bool PREP>
 __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
   constexpr bool SHARED = SCAT == SC_SHARED;
   constexpr bool WARPC = SCAT == SC_WARP && MODE == TS_GRAD;
+  constexpr int TS_STAGES = ts_stages<T, MODE>();
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr uint32_t kConnBytes = TS_THREADS * 16u;
   constexpr uint32_t kGBytes = TS_THREADS * 12u * sizeof(T);
@@ -300,8 +303,9 @@ kg_status logtab_for_device(const float4** out) {
   return KG_OK;
 }
 
-template <typename T, bool PAIR, bool SHARED>
+template <typename T, bool PAIR, bool SHARED, int MODE>
 static size_t ts_smem() {
+  constexpr int TS_STAGES = ts_stages<T, MODE>();
   return (size_t)TS_STAGES * (TS_THREADS * 16 + TS_THREADS * 12 * sizeof(T)) +
          2 * TS_STAGES * sizeof(uint64_t) + (PAIR ? kLogTableSize * sizeof(float4) : 0) +
          (2 * TS_WARPS + 2) * sizeof(double) +
@@ -351,7 +355,7 @@ kg_status tet_staged_setup(kg_problem* p) {
 template <typename T, bool PAIR, int MODE, int SCAT, bool PREP>
 static cudaError_t launch_ts_k(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
   auto kern = tet_staged_kernel<T, PAIR, MODE, SCAT, PREP>;
-  const size_t smem = ts_smem<T, PAIR, SCAT == SC_SHARED>();
+  const size_t smem = ts_smem<T, PAIR, SCAT == SC_SHARED, MODE>();
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   static int occ = 0;
