@@ -93,6 +93,74 @@ int kgo_quadform_grad(int64_t m, int64_t n, const double *A, const double *x,
   return 0;
 }
 
+/* ------------------------------------------------ sparse ||A x||^2 ------ */
+/* A is m x n in compressed sparse rows: the entries of row i are
+ * val[p] at column col[p] for rowptr[i] <= p < rowptr[i+1]; a column may repeat
+ * within a row (the entries then add).  The forward pass is the same
+ * team-nested parallel_reduce as the dense case with the inner loop over the
+ * stored entries only: a read of x through the index map col (Sec. 3.3), whose
+ * reverse is a scatter-add into xbar. */
+static int check_csr(int64_t m, int64_t n, int64_t nnz, const int32_t *rowptr,
+                     const int32_t *col) {
+  if (m < 0 || n < 0 || nnz < 0 || !rowptr) return -1;
+  if (rowptr[0] != 0 || rowptr[m] != nnz) return -3;
+  for (int64_t i = 0; i < m; ++i)
+    if (rowptr[i + 1] < rowptr[i]) return -3;
+  for (int64_t p = 0; p < nnz; ++p)
+    if (col[p] < 0 || col[p] >= n) return -3;
+  return 0;
+}
+
+/* Forward: y_i = sum_{p in row i} val[p] x[col[p]] ; f = sum_i y_i^2.  y may be NULL. */
+int kgo_spquadform_value(int64_t m, int64_t n, int64_t nnz, const int32_t *rowptr,
+                         const int32_t *col, const double *val, const double *x, double *y,
+                         double *f) {
+  int rc = check_csr(m, n, nnz, rowptr, col);
+  if (rc) return rc;
+  if (!f || (nnz > 0 && (!val || !x))) return -1;
+  nsum tot = {0, 0};
+  for (int64_t i = 0; i < m; ++i) {
+    nsum yi = {0, 0};
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) nadd(&yi, val[p] * x[col[p]]);
+    double v = nval(&yi);
+    if (y) y[i] = v;
+    nadd(&tot, v * v);
+  }
+  *f = nval(&tot);
+  return 0;
+}
+
+/* Value and gradient with output adjoint fbar.  Reverse of the forward above:
+ * ybar_i = 2 y_i fbar (broadcast of the reduction adjoint); every read
+ * val[p] * x[col[p]] becomes xbar[col[p]] += val[p] ybar_i (the scatter-add of
+ * the gathered x) and valbar[p] = x[col[p]] ybar_i.  gx (n) is overwritten;
+ * gval (nnz) is overwritten when non-NULL. */
+int kgo_spquadform_grad(int64_t m, int64_t n, int64_t nnz, const int32_t *rowptr,
+                        const int32_t *col, const double *val, const double *x, double fbar,
+                        double *f, double *gx, double *gval) {
+  int rc = check_csr(m, n, nnz, rowptr, col);
+  if (rc) return rc;
+  if (n > 0 && !gx) return -1;
+  double *y = (double *)malloc((size_t)(m > 0 ? m : 1) * sizeof(double));
+  nsum *acc = (nsum *)calloc((size_t)(n > 0 ? n : 1), sizeof(nsum));
+  if (!y || !acc) { free(y); free(acc); return -2; }
+  double fv = 0;
+  rc = kgo_spquadform_value(m, n, nnz, rowptr, col, val, x, y, &fv);
+  if (rc) { free(y); free(acc); return rc; }
+  if (f) *f = fv;
+  for (int64_t i = 0; i < m; ++i) {
+    double ybar = 2.0 * y[i] * fbar;
+    for (int64_t p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+      nadd(&acc[col[p]], val[p] * ybar);
+      if (gval) gval[p] = x[col[p]] * ybar;
+    }
+  }
+  for (int64_t j = 0; j < n; ++j) gx[j] = nval(&acc[j]);
+  free(y);
+  free(acc);
+  return 0;
+}
+
 /* ----------------------------------------------------- tet energy ------- */
 /* Per-element forward quantities of f(u) = sum_e log1p(|G_e u_e|^2):
  * u_e = (u[conn[e][0..3]]) is a gather through the index map conn, and

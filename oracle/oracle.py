@@ -54,6 +54,8 @@ def _load():
                 "kgo_tet_adjoint_local": [i64, i64, ip, dp, dp, d, dp],
                 "kgo_tet_grad": [i64, i64, ip, dp, dp, d, dp, dp],
                 "kgo_tet_descent": [i64, i64, ip, dp, dp, d, ctypes.c_int, dp],
+                "kgo_spquadform_value": [i64, i64, i64, ip, ip, dp, dp, dp, dp],
+                "kgo_spquadform_grad": [i64, i64, i64, ip, ip, dp, dp, d, dp, dp, dp],
                 "kgo_laplace1d_value": [i64, dp, dp, dp],
                 "kgo_laplace1d_grad": [i64, dp, dp, d, dp, dp, dp],
             }
@@ -102,6 +104,32 @@ def quadform_grad(A, x, fbar=1.0, want_gA=False):
     _check(_load().kgo_quadform_grad(m, n, _p(A), _p(x), float(fbar), _p(f), _p(gx), _p(gA)),
            "quadform_grad")
     return (float(f[0]), gx, gA) if want_gA else (float(f[0]), gx)
+
+
+# ------------------------------------------------------------ sparse ||A x||^2
+def spquadform_value(rowptr, col, val, x, n=None, return_y=False):
+    rowptr, col, val, x = _i32(rowptr), _i32(col), _f64(val), _f64(x)
+    m = rowptr.shape[0] - 1
+    n = x.shape[0] if n is None else n
+    y = np.empty(max(m, 1))
+    f = np.zeros(1)
+    _check(_load().kgo_spquadform_value(m, n, col.shape[0], _p(rowptr), _p(col), _p(val), _p(x),
+                                        _p(y), _p(f)), "spquadform_value")
+    return (float(f[0]), y[:m]) if return_y else float(f[0])
+
+
+def spquadform_grad(rowptr, col, val, x, fbar=1.0, want_gval=False):
+    """Returns (f, gx) or (f, gx, gval) for A in CSR form (rowptr, col, val), A m x len(x)."""
+    rowptr, col, val, x = _i32(rowptr), _i32(col), _f64(val), _f64(x)
+    m, n = rowptr.shape[0] - 1, x.shape[0]
+    f = np.zeros(1)
+    gx = np.empty(max(n, 1))
+    gval = np.empty(max(col.shape[0], 1)) if want_gval else None
+    _check(_load().kgo_spquadform_grad(m, n, col.shape[0], _p(rowptr), _p(col), _p(val), _p(x),
+                                       float(fbar), _p(f), _p(gx), _p(gval)), "spquadform_grad")
+    if want_gval:
+        return float(f[0]), gx[:n], gval[:col.shape[0]]
+    return float(f[0]), gx[:n]
 
 
 # ------------------------------------------------------------ tet energy

@@ -14,6 +14,11 @@ Workloads (all synthetic, seeded with numpy ``Generator(PCG64(seed))``):
   functions of element e (column k = grad lambda_k); it is input data computed
   from the vertex coordinates, exactly (adjugate / determinant) when the
   coordinates are integers.
+* sparse quadratic form f(x) = ||A x||^2 with A in compressed sparse rows: row i
+  holds d_i ~ U{d_lo, ..., d_hi} entries at uniformly random columns (sorted
+  within the row; a column may repeat, the entries then add), values
+  N(0, 1/d_i); x uniform on [-1, 1].  Degrees, then columns, then values, then
+  x are drawn in that order.
 * the paper's 1-D example (Section 4, Fig. "function_f"): x and b uniform on
   [-1, 1].
 * batched mixes: sizes n_k = round(exp(U[ln 32, ln 2048])) (seed 3) and tet
@@ -66,6 +71,45 @@ class TetMesh:
     @property
     def nv(self) -> int:
         return int(self.coords.shape[0])
+
+
+@dataclass
+class CsrMatrix:
+    rowptr: np.ndarray  # int32 [m + 1]
+    col: np.ndarray     # int32 [nnz]
+    val: np.ndarray     # float64 [nnz]
+    m: int
+    n: int
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.shape[0])
+
+    def dense(self) -> np.ndarray:
+        """The m x n matrix (repeated columns add)."""
+        A = np.zeros((self.m, self.n))
+        rows = np.repeat(np.arange(self.m), np.diff(self.rowptr))
+        np.add.at(A, (rows, self.col), self.val)
+        return A
+
+
+def spquadform_inputs(m: int = 1 << 20, n: int | None = None, d_lo: int = 8, d_hi: int = 24,
+                      seed: int = 7):
+    """Random CSR matrix (see the module docstring) and x; returns (CsrMatrix, x)."""
+    n = m if n is None else n
+    rng = _rng(seed)
+    deg = rng.integers(d_lo, d_hi + 1, m)
+    rowptr = np.zeros(m + 1, np.int64)
+    np.cumsum(deg, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    if nnz >= 2 ** 31:
+        raise ValueError("nnz must be < 2^31")
+    col = rng.integers(0, n, nnz)
+    rows = np.repeat(np.arange(m), deg)
+    col = col[np.lexsort((col, rows))]  # sorted within each row
+    val = rng.standard_normal(nnz) / np.sqrt(np.repeat(deg, deg))
+    x = rng.uniform(-1.0, 1.0, n)
+    return CsrMatrix(rowptr.astype(np.int32), col.astype(np.int32), val, m, n), x
 
 
 def _grid_conn(a: int, b: int, c: int) -> np.ndarray:

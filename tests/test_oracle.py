@@ -119,6 +119,88 @@ def test_quadform_empty():
     assert f == 0.0 and np.array_equal(gx, np.zeros(4))
 
 
+# ------------------------------------------------------------------ sparse (CSR)
+def _small_csr(seed=11, m=9, n=7):
+    A, x = W.spquadform_inputs(m, n, d_lo=0, d_hi=5, seed=seed)
+    return A, x
+
+
+def test_spquadform_closed_form_with_repeats_and_empty_rows():
+    # grad = 2 fbar A^T (A x) on the densified matrix (numpy), valbar_p = 2 fbar y_i x_col(p)
+    for seed in (11, 12, 13):
+        A, x = _small_csr(seed)
+        D = A.dense()
+        y = D @ x
+        f, gx, gval = O.spquadform_grad(A.rowptr, A.col, A.val, x, fbar=0.75, want_gval=True)
+        assert f == pytest.approx(float(y @ y), rel=1e-14)
+        assert rel(gx, 1.5 * D.T @ y) < 1e-14
+        rows = np.repeat(np.arange(A.m), np.diff(A.rowptr))
+        assert rel(gval, 1.5 * y[rows] * x[A.col]) < 1e-14
+
+
+def test_spquadform_repeated_column_adds():
+    # a row storing column 2 twice (values a, b) behaves as one entry a + b
+    rowptr = np.array([0, 3, 4], np.int32)
+    col = np.array([2, 2, 0, 1], np.int32)
+    val = np.array([0.5, -2.0, 1.0, 3.0])
+    x = np.array([0.25, -1.0, 4.0])
+    f, gx = O.spquadform_grad(rowptr, col, val, x)
+    D = np.array([[1.0, 0.0, -1.5], [0.0, 3.0, 0.0]])
+    assert f == (D @ x) @ (D @ x)
+    assert np.array_equal(gx, 2 * D.T @ (D @ x))
+
+
+def test_spquadform_equals_dense_oracle_on_dense_pattern():
+    # every entry stored, in column order: the sparse forward is the dense one entry for entry
+    A, x = W.quadform_inputs(6, m=5, seed=2)
+    rowptr = np.arange(0, 31, 6, dtype=np.int32)
+    col = np.tile(np.arange(6, dtype=np.int32), 5)
+    fs, gs = O.spquadform_grad(rowptr, col, A.ravel(), x)
+    fd, gd = O.quadform_grad(A, x)
+    assert fs == fd and np.array_equal(gs, gd)
+
+
+def test_spquadform_exact_rational():
+    rowptr = np.array([0, 2, 2, 5], np.int32)
+    col = np.array([0, 3, 1, 1, 2], np.int32)
+    val = np.array([1.0, 2.0, 3.0, -1.0, 0.5])
+    x = np.array([1.0, 2.0, 3.0, 4.0])
+    f, gx, gval = O.spquadform_grad(rowptr, col, val, x, want_gval=True)
+    # y = (1 + 8, 0, 6 - 2 + 1.5) = (9, 0, 5.5); f = 81 + 30.25
+    assert f == 111.25
+    assert np.array_equal(gx, [18.0, 22.0, 5.5, 36.0])
+    assert np.array_equal(gval, [18.0, 72.0, 22.0, 22.0, 33.0])
+
+
+def test_spquadform_dual_numbers_in_x_and_val():
+    A, x = _small_csr(14, m=6, n=5)
+    f, gx, gval = O.spquadform_grad(A.rowptr, A.col, A.val, x, want_gval=True)
+
+    def f_dual(val, xv):
+        tot = 0.0
+        for i in range(A.m):
+            yi = 0.0
+            for p in range(A.rowptr[i], A.rowptr[i + 1]):
+                yi = yi + val[p] * xv[A.col[p]]
+            tot = tot + yi * yi
+        return tot
+
+    for j in range(A.n):
+        assert f_dual(list(A.val), seed(x, j)).d == pytest.approx(gx[j], rel=1e-13, abs=1e-14)
+    for p in range(A.nnz):
+        assert f_dual(seed(A.val, p), list(x)).d == pytest.approx(gval[p], rel=1e-13, abs=1e-14)
+
+
+def test_spquadform_empty_and_rejects_bad_structure():
+    f, gx = O.spquadform_grad(np.zeros(4, np.int32), np.zeros(0, np.int32), np.zeros(0), np.ones(3))
+    assert f == 0.0 and np.array_equal(gx, np.zeros(3))
+    with pytest.raises(ValueError):  # column out of range
+        O.spquadform_grad(np.array([0, 1], np.int32), np.array([3], np.int32), np.ones(1), np.ones(3))
+    with pytest.raises(ValueError):  # decreasing rowptr
+        O.spquadform_grad(np.array([0, 2, 1, 2], np.int32), np.array([0, 1], np.int32), np.ones(2),
+                          np.ones(3))
+
+
 # ------------------------------------------------------------------ tets
 def _ref_tet():
     rows = [l for l in open(os.path.join(GOLDEN, "single_tet_reference.txt"))
@@ -360,6 +442,8 @@ def test_pins_catch_planted_mistakes(tmp_path):
                           "c[e * 4 + k] = G[e * 12 + 0 * 4 + (3 - k)] * gbar[0]"),
         "lap_missing_guard": ("if (j != n - 1) x3bar[j + 1] -= ybar;",
                               "if (j + 1 < n) x3bar[j + 1] += ybar;"),
+        "sp_scatter_to_row": ("nadd(&acc[col[p]], val[p] * ybar);", "nadd(&acc[i % n], val[p] * ybar);"),
+        "sp_gather_first_col": ("nadd(&yi, val[p] * x[col[p]]);", "nadd(&yi, val[p] * x[col[rowptr[i]]]);"),
     }
     for name, (old, new) in mutants.items():
         assert old in src, name
@@ -378,6 +462,14 @@ def test_pins_catch_planted_mistakes(tmp_path):
             lib.kgo_quadform_grad(ctypes.c_int64(A.shape[0]), ctypes.c_int64(A.shape[1]), p(A), p(x),
                                   ctypes.c_double(1.0), p(f), p(gx), None)
             caught = rel(gx, 2 * A.T @ (A @ x)) > 1e-6
+        elif name.startswith("sp_"):
+            A, x = _small_csr(15, m=8, n=6)
+            f, gx = np.zeros(1), np.empty(A.n)
+            lib.kgo_spquadform_grad(ctypes.c_int64(A.m), ctypes.c_int64(A.n), ctypes.c_int64(A.nnz),
+                                    p(A.rowptr), p(A.col), p(A.val), p(x), ctypes.c_double(1.0),
+                                    p(f), p(gx), None)
+            D = A.dense()
+            caught = rel(gx, 2 * D.T @ (D @ x)) > 1e-6
         elif name.startswith("tet"):
             conn, G = _ref_tet()
             u = np.array([0.3, -0.7, 0.25, 0.9])
