@@ -203,6 +203,79 @@ class DenseWL(Workload):
         return done / 1e9 / dt, f"{reps} x full {self.m}x{self.n} value+grad (oracle, 1 thread)"
 
 
+class SparseWL(Workload):
+    """Sparse ||Ax||^2, A 2^20 x 2^20 in CSR with 8..24 stored entries per row."""
+
+    def __init__(self, m, dtype, strategy="auto"):
+        self.m = m
+        self.dtype = dtype
+        self.dtype_name = dtype
+        self.es = 8 if dtype == "f64" else 4
+        self.strategy = strategy
+        self.arith = "native"
+
+    def setup(self, dev):
+        import torch
+        from paper_2507_13204_gb300 import api, workloads as W
+        A, x = W.spquadform_inputs(self.m)
+        td = torch.float64 if self.dtype == "f64" else torch.float32
+        if self.dtype == "f32":
+            A.val = A.val.astype("float32").astype("float64")
+            x = x.astype("float32").astype("float64")
+        self.A, self.x_host, self.n, self.nnz = A, x, A.n, A.nnz
+        self.rp = torch.tensor(A.rowptr, device=dev)
+        self.cl = torch.tensor(A.col, device=dev)
+        self.vl = torch.tensor(A.val, dtype=td, device=dev)
+        self.xt = torch.tensor(x, dtype=td, device=dev)
+        self.p = api.SpQuadForm(self.rp, self.cl, self.vl, self.n, strategy=self.strategy)
+        self.gx = torch.empty(self.n, dtype=td, device=dev)
+        self.f = torch.empty((), dtype=td, device=dev)
+        self.fe = torch.empty((), dtype=td, device=dev)
+        self.x_pin = torch.tensor(x, dtype=td).pin_memory()
+        self.g_pin = torch.empty(self.n, dtype=td).pin_memory()
+        self.f_pin = torch.empty((), dtype=td).pin_memory()
+
+    def step(self):
+        self.p.grad(self.xt, gx=self.gx, f=self.f)
+
+    def eval_step(self):
+        self.p.eval(self.xt, f=self.fe)
+
+    def e2e_step(self):
+        self.p.grad_host(self.x_pin, self.g_pin, self.f_pin)
+
+    @property
+    def grad_bytes(self):  # the CSR matrix once, x in, gradient out
+        return 4 * (self.m + 1) + (4 + self.es) * self.nnz + 2 * self.es * self.n
+
+    def dominant(self):
+        if self.p.config[0] == "transpose":  # the column gather: CSC once, y in, gradient out
+            return (4 * (self.n + 1) + (4 + self.es) * self.nnz + self.es * (self.m + self.n), None)
+        return (self.grad_bytes, None)
+
+    def h2d_d2h(self):
+        return self.es * self.n, self.es * (self.n + 1)
+
+    def config(self):
+        return {"workload": f"sparse ||Ax||^2, A {self.m}x{self.n} CSR, 8..24 entries per row at "
+                            f"uniform random columns ({self.nnz} stored), {self.dtype.upper()}, "
+                            f"value+grad wrt x",
+                "strategy": self.strategy, "arith": self.arith,
+                "l2": "inputs larger than L2 (CSR > 129 MB)"}
+
+    def oracle_sample(self, budget_s=10.0):
+        from oracle import oracle as O
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            O.spquadform_grad(self.A.rowptr, self.A.col, self.A.val, self.x_host)
+            reps += 1
+            if time.perf_counter() - t0 >= budget_s or reps >= 20:
+                break
+        dt = time.perf_counter() - t0
+        return reps * self.grad_bytes / 1e9 / dt, f"{reps} x full value+grad (oracle, 1 thread)"
+
+
 class TetWL(Workload):
     def __init__(self, a, dtype, strategy="auto", arith="auto"):
         self.a = a
@@ -557,6 +630,10 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
         return TetWL(size or 100, "f32", strategy=strategy or "auto")
     if name == "tetcsr":
         return TetWL(size or 100, "f64", strategy="csr", arith=arith)
+    if name == "sparse":
+        return SparseWL(size or (1 << 20), "f64", strategy=strategy or "auto")
+    if name == "sparse32":
+        return SparseWL(size or (1 << 20), "f32", strategy=strategy or "auto")
     if name == "laplace":
         return LaplaceWL(size or 10000)
     if name == "laplace_atomic":
@@ -634,9 +711,10 @@ def main():
                     help="problem size override (dense n, tet cubes per axis, 1-D n) for small "
                          "profiling cases; the default is the full workload")
     ap.add_argument("--rows", type=int, default=0, help="dense: rows of A (default: square)")
-    ap.add_argument("--strategy", default="", choices=["", "atomic", "shared", "warp", "csr"],
-                    help="tet, batched: reverse-pass scatter strategy (default: the library's "
-                         "choice)")
+    ap.add_argument("--strategy", default="", choices=["", "atomic", "shared", "warp", "csr",
+                                                       "transpose"],
+                    help="tet, batched, sparse: reverse-pass scatter strategy (default: the "
+                         "library's choice)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -897,6 +975,15 @@ def run_reference(args, rank, world):
         fn = lambda: O.tet_grad(conn, G, u)
         sample = f"value+grad of the first {ne} tets of the {wl.a}^3 mesh per step"
         to_value = lambda s: unit_bytes / 1e9 / s
+    elif isinstance(wl, SparseWL):
+        A, x = W.spquadform_inputs(wl.m)
+        if wl.dtype == "f32":
+            A.val = A.val.astype("float32").astype("float64")
+            x = x.astype("float32").astype("float64")
+        wl.A, wl.n, wl.nnz = A, A.n, A.nnz
+        fn = lambda: O.spquadform_grad(A.rowptr, A.col, A.val, x)
+        sample = f"one full value+grad of the {A.m}x{A.n} CSR problem per step"
+        to_value = lambda s: wl.grad_bytes / 1e9 / s
     else:
         x, b = W.laplace1d_inputs(wl.n)
         fn = lambda: O.laplace1d_grad(x, b)

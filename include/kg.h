@@ -24,6 +24,11 @@
  *   KG_TETENERGY  f(u; conn, G) = sum_e log1p(|G_e u_e|^2): u_e gathers the 4
  *                 vertex values of tet e through conn (an index map), G_e is
  *                 the 3x4 matrix of P1 barycentric gradients.
+ *   KG_SPQUADFORM f(x; A) = ||A x||^2, A sparse m x n in compressed sparse
+ *                 rows (rowptr, col, val): the row loop runs over the stored
+ *                 entries only and reads x through the index map col, so the
+ *                 reverse pass is a scatter-add (or, rescheduled, a gather
+ *                 over the transpose).
  *   KG_LAPLACE1D  the paper's example (Sec. 4, Fig. "function_f"):
  *                 f(x, b) = ||A (3 x) - b||^2, A = tridiag(-1, 2, -1).
  *
@@ -76,7 +81,7 @@ typedef enum {
                              the results of that call are invalid (rerun with KG_ARITH_NATIVE) */
 } kg_status;
 
-typedef enum { KG_QUADFORM = 1, KG_TETENERGY = 2, KG_LAPLACE1D = 3 } kg_kind;
+typedef enum { KG_QUADFORM = 1, KG_TETENERGY = 2, KG_LAPLACE1D = 3, KG_SPQUADFORM = 4 } kg_kind;
 typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
 
 /* Reverse-pass schedule for gathers (Sec. 3.3 and Sec. 5).
@@ -85,6 +90,9 @@ typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
  *             vertex gathers its incident entries through the transposed
  *             connectivity built at kg_create; bitwise run-to-run reproducible.
  *   TRANSPOSE (dense) a second kernel reads A by columns: xbar = A^T ybar.
+ *             (sparse) atomic-free: a row kernel stores y, then a team per
+ *             column of the transpose (built at kg_create) gathers
+ *             xbar_j = 2 fbar sum_i a_ij y_i in ascending i; reproducible.
  *   FUSED     (dense) one pass over A: each team computes y_i, broadcasts
  *             ybar_i and accumulates ybar_i A_i,: into private partials that a
  *             second tiny kernel sums in a fixed order; reproducible.
@@ -96,7 +104,8 @@ typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
  *             each warp: lanes whose element shares a vertex (in the same local
  *             slot) add their values by shuffles and one lane issues the
  *             atomic.
- *   AUTO      FUSED for dense, WARP for tets, the stencil transpose for 1-D. */
+ *   AUTO      FUSED for dense, WARP for tets, ATOMIC for sparse, the stencil
+ *             transpose for 1-D. */
 typedef enum {
   KG_STRATEGY_AUTO = 0,
   KG_STRATEGY_ATOMIC = 1,
@@ -154,14 +163,20 @@ void kg_options_default(kg_options *opt);
  * allocated once, here, never inside the per-call entry points).
  *   kind   kg_kind.
  *   sizes  KG_QUADFORM: {n} (square) or {m, n};  KG_TETENERGY: {N_e, N_v};
- *          KG_LAPLACE1D: {n}.  All sizes >= 1 and < 2^31.
+ *          KG_LAPLACE1D: {n};  KG_SPQUADFORM: {m, n, nnz}.  All sizes >= 1
+ *          and < 2^31 (nnz may be 0).
  *   data   device pointers, borrowed: KG_QUADFORM {A (m*n, row-major)};
  *          KG_TETENERGY {conn (int32, N_e*4), G (N_e*12, row-major 3x4 per
  *          element: G[e*12 + r*4 + k] = d lambda_k / d x_r)};
- *          KG_LAPLACE1D {b (n)}.  Each must be 16-byte aligned.
+ *          KG_LAPLACE1D {b (n)};  KG_SPQUADFORM {rowptr (int32, m+1),
+ *          col (int32, nnz, each in [0, n), repeats add), val (nnz)}.  A, conn,
+ *          G and b must be 16-byte aligned; the sparse arrays element-aligned.
  *   opt    NULL for defaults.
- * Validates conn against [0, N_v) (KG_ERR_BOUNDS), builds the transposed
- * connectivity when the CSR strategy is selected, and synchronises `s`. */
+ * Validates conn against [0, N_v) and the CSR structure (rowptr[0] = 0,
+ * rowptr[m] = nnz, non-decreasing, columns in [0, n)) (KG_ERR_BOUNDS), builds
+ * the transposed connectivity (tet CSR strategy) or the transposed matrix
+ * (sparse TRANSPOSE strategy, values copied in column order), and synchronises
+ * `s`. */
 kg_status kg_create(kg_problem **out, int kind, const int64_t *sizes, int nsizes,
                     const void *const *data, int ndata, const kg_options *opt, kg_stream s);
 
@@ -174,7 +189,8 @@ kg_status kg_eval(kg_problem *p, const void *x, void *f, kg_stream s);
  *   f      nullable; receives f(x).
  *   gx     gradient w.r.t. x, length n or N_v.
  *   gdata  nullable; gradient w.r.t. the first data operand: A (m*n,
- *          QUADFORM) or b (n, LAPLACE1D).  KG_ERR_UNSUPPORTED for TET.
+ *          QUADFORM), b (n, LAPLACE1D) or the stored values val (nnz,
+ *          SPQUADFORM).  KG_ERR_UNSUPPORTED for TET.
  *   seed   nullable device scalar: the output adjoint fbar (NULL means 1).
  *   accumulate  0: gx/gdata are overwritten; 1: the gradient is added to
  *          them (the "_d_x +=" convention of the generated code). */

@@ -18,7 +18,7 @@ KG_OK, KG_ERR_INVALID_ARG, KG_ERR_OOM, KG_ERR_CUDA, KG_ERR_BOUNDS, KG_ERR_TIMEOU
     KG_ERR_UNSUPPORTED, KG_ERR_STATE, KG_ERR_RANGE = range(9)
 STATUS_NAMES = ["KG_OK", "KG_ERR_INVALID_ARG", "KG_ERR_OOM", "KG_ERR_CUDA", "KG_ERR_BOUNDS",
                 "KG_ERR_TIMEOUT", "KG_ERR_UNSUPPORTED", "KG_ERR_STATE", "KG_ERR_RANGE"]
-KG_QUADFORM, KG_TETENERGY, KG_LAPLACE1D = 1, 2, 3
+KG_QUADFORM, KG_TETENERGY, KG_LAPLACE1D, KG_SPQUADFORM = 1, 2, 3, 4
 KG_F64, KG_F32 = 0, 1
 KG_STRATEGY_AUTO, KG_STRATEGY_ATOMIC, KG_STRATEGY_CSR, KG_STRATEGY_TRANSPOSE, KG_STRATEGY_FUSED, \
     KG_STRATEGY_SHARED, KG_STRATEGY_WARP = range(7)

@@ -107,6 +107,27 @@ class QuadForm(Problem):
         return self.n
 
 
+class SpQuadForm(Problem):
+    """f(x) = ||A x||^2, A (m x n) sparse in compressed sparse rows on the device:
+    rowptr int32 [m + 1], col int32 [nnz], val [nnz].  gdata of grad() is the
+    gradient w.r.t. val."""
+    kind = L.KG_SPQUADFORM
+
+    def __init__(self, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor, n: int, **kw):
+        rowptr = _dev_tensor(rowptr, torch.int32)
+        col = _dev_tensor(col, torch.int32)
+        val = _dev_tensor(val)
+        if col.shape[0] != val.shape[0] or rowptr.dim() != 1:
+            raise ValueError("kg: col and val must have nnz entries, rowptr m + 1")
+        m, nnz = int(rowptr.shape[0]) - 1, int(col.shape[0])
+        super().__init__([m, n, nnz], [rowptr, col, val], val.dtype, **kw)
+        self.m, self.n, self.nnz = m, int(n), nnz
+
+    @property
+    def nx(self):
+        return self.n
+
+
 class TetEnergy(Problem):
     """f(u) = sum_e log1p(|G_e u_e|^2); conn int32 [N_e, 4], G [N_e, 12]."""
     kind = L.KG_TETENERGY

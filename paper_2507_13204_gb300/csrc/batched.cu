@@ -142,7 +142,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
     xbn[k] = T(0);
   }
   Acc fp = acc_zero();
-  double fn = 0.0;
+  FSum<T> fn;
   const int64_t r1 = w.start + w.count;
   const int iters = (w.count + NT - 1) / NT;
   // software pipeline: the next row's loads are in flight while this row computes
@@ -222,7 +222,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
         for (int q = 1; q < TW; ++q) d += rt[q];
       }
       if (valid) {
-        fn += (double)d * (double)d;
+        fn.add(d);
         const T yb = T(2) * d;
 #pragma unroll
         for (int k = 0; k < B_CPT; ++k)
@@ -280,7 +280,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
       }
     }
     __syncthreads();
-    if (lt == 0) red[team] = fn;
+    if (lt == 0) red[team] = fn.get();
     __syncthreads();
     double tot = 0.0;
     for (int t2 = 0; t2 < NT; ++t2) tot += red[t2];

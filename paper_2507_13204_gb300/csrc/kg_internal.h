@@ -53,9 +53,12 @@ struct kg_problem {
   int strategy = KG_STRATEGY_AUTO;  // resolved strategy
   int mode = KG_MODE_RECOMPUTE;     // resolved mode
   int arith = KG_ARITH_NATIVE;      // resolved FP64 arithmetic
-  int64_t m = 0, n = 0;             // QUADFORM m x n; TET m = N_e, n = N_v; LAPLACE1D n
-  const void* data0 = nullptr;      // A | conn | b
-  const void* data1 = nullptr;      // - | G | -
+  int64_t m = 0, n = 0;             // QUADFORM m x n; TET m = N_e, n = N_v; LAPLACE1D n;
+                                    // SPQUADFORM m x n
+  int64_t nnz = 0;                  // SPQUADFORM stored entries
+  const void* data0 = nullptr;      // A | conn | b | rowptr
+  const void* data1 = nullptr;      // - | G | - | col
+  const void* data2 = nullptr;      // - | - | - | val
   size_t esize = 8;
 
   // workspaces
@@ -70,14 +73,16 @@ struct kg_problem {
   void* tape = nullptr;      // tet: c_e [N_e][4]
   void* aprep = nullptr;     // FP64 pair: A (dense) or G (tet) split into float pairs
   bool tape_valid = false;
-  int* rowptr = nullptr;     // tet CSR: [N_v + 1]
-  int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k
+  int* rowptr = nullptr;     // tet CSR: [N_v + 1]; sparse CSC: colptr [n + 1]
+  int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k; sparse CSC: row of each entry
+  void* valT = nullptr;      // sparse CSC: values in column order
   void* xdev = nullptr;      // kg_grad_host staging
   void* gdev = nullptr;
   void* fdev = nullptr;
 
   kg::QfConfig qf;           // dense launch configuration
   int tet_block = 256, tet_grid = 1;
+  int sq_team = 8, sq_col_team = 8;  // sparse: lanes per row team / per column team
   cudaStream_t last_stream = nullptr;
 };
 
@@ -127,6 +132,16 @@ kg_status tet_grad(kg_problem* p, const void* x, void* f, void* gx, const void* 
                    int accumulate, cudaStream_t s);
 kg_status tet_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,
                              cudaStream_t s);
+
+// Buckets of positions by key (transposed index lists; tet.cu), synchronises s.
+kg_status build_buckets(const int* keys, int64_t count, int nbins, int* binptr, int* perm,
+                        cudaStream_t s);
+
+// sparse ||A x||^2 (spquadform.cu)
+kg_status spq_setup(kg_problem* p, cudaStream_t s);
+kg_status spq_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
+kg_status spq_grad(kg_problem* p, const void* x, void* f, void* gx, void* gval, const void* seed,
+                   int accumulate, cudaStream_t s);
 
 kg_status lap_setup(kg_problem* p, cudaStream_t s);
 kg_status lap_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);

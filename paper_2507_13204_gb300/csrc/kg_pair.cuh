@@ -150,6 +150,28 @@ __host__ __device__ __forceinline__ Acc acc_add(Acc a, Acc b) {
   return c;
 }
 
+// Sum of the per-row squares y_i^2 that make f: in double for FP64 data; for
+// FP32 data a float sum with its exact rounding error (TwoSum), so that FP32
+// kernels issue no FP64 instruction per row (one FP64 instruction occupies
+// GB300's narrow FP64 unit for the whole warp, however few lanes are active).
+template <typename T>
+struct FSum {
+  double v = 0.0;
+  __device__ __forceinline__ void add(T y) { v += (double)y * (double)y; }
+  __device__ __forceinline__ double get() const { return v; }
+};
+template <>
+struct FSum<float> {
+  float s = 0.f, l = 0.f;
+  __device__ __forceinline__ void add(float y) {
+    float t, e;
+    two_sum(s, y * y, t, e);
+    s = t;
+    l += e;
+  }
+  __device__ __forceinline__ double get() const { return (double)s + (double)l; }
+};
+
 // Normalised pair (|l| <= ulp(h)/2) of an accumulator.
 __host__ __device__ __forceinline__ Pair acc_pair(Acc a) {
   Pair p;

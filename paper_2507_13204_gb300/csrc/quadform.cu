@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(512) qf_team_kernel(QfArgs<T> a) {
   T xb[CPT_MAX];
 #pragma unroll
   for (int k = 0; k < CPT_MAX; ++k) xb[k] = T(0);
-  double fsum = 0.0;
+  FSum<T> fsum;
 
   const int64_t r0 = (int64_t)blockIdx.x * a.rows_per_cta;
   const int64_t r1 = r0 + a.rows_per_cta < a.m ? r0 + a.rows_per_cta : a.m;
@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(512) qf_team_kernel(QfArgs<T> a) {
     const T yv = team_sum<T, TEAM>(d, red, it & 1);
     if (valid) {
       if (lt == 0) {
-        fsum += (double)yv * (double)yv;
+        fsum.add(yv);
         if (a.y) a.y[row] = yv;
       }
       if constexpr (MODE == QF_FUSED) {
@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(512) qf_team_kernel(QfArgs<T> a) {
 
   // CTA's f partial: team leaders in team order.
   __syncthreads();
-  if (lt == 0) fs[team] = fsum;
+  if (lt == 0) fs[team] = fsum.get();
   __syncthreads();
   double fcta = 0.0;
   for (int t = 0; t < nteams; ++t) fcta += fs[t];

@@ -15,6 +15,7 @@
 
 #include "kg_device.cuh"
 #include "kg_internal.h"
+#include "kg_pair.cuh"
 
 namespace kg {
 
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(QF_CT, 2) qf_f32_kernel(Qf32Args a) {
   float4 xb[QPT];
 #pragma unroll
   for (int k = 0; k < QPT; ++k) xb[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-  double fsum = 0.0;
+  FSum<float> fsum;
 
   for (int it = 0; it < nrows; ++it) {
     const int s = it & 1;
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(QF_CT, 2) qf_f32_kernel(Qf32Args a) {
     float y = 0.f;
 #pragma unroll
     for (int q = 0; q < QF_CW; ++q) y += red[(it & 1) * QF_CW + q];
-    if (t == 0) fsum += (double)y * (double)y;
+    if (t == 0) fsum.add(y);
     if (FUSED) {
       const float yb = fb2 * y;
 #pragma unroll
@@ -157,9 +158,9 @@ __global__ void __launch_bounds__(QF_CT, 2) qf_f32_kernel(Qf32Args a) {
       const int jq = t + QF_CT * k;
       if (jq < nq) out[jq] = xb[k];
     }
-    if (t == 0) a.fpart[blockIdx.x] = fsum;
+    if (t == 0) a.fpart[blockIdx.x] = fsum.get();
   } else if (t == 0) {
-    a.fpart[blockIdx.x] = fsum;
+    a.fpart[blockIdx.x] = fsum.get();
     __threadfence();
     if (atomicAdd(a.counter, 1u) == gridDim.x - 1) {
       __threadfence();

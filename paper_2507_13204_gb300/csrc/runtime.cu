@@ -183,9 +183,11 @@ kg_status kg_create(kg_problem** out, int kind, const int64_t* sizes, int nsizes
   if (!out) return fail(KG_ERR_INVALID_ARG, "kg_create: out is NULL");
   *out = nullptr;
   if (!sizes || nsizes < 1) return fail(KG_ERR_INVALID_ARG, "kg_create: sizes missing");
-  for (int i = 0; i < nsizes; ++i)
-    if (sizes[i] < 1 || sizes[i] >= (int64_t(1) << 31))
-      return fail(KG_ERR_INVALID_ARG, "kg_create: every size must be in [1, 2^31)");
+  for (int i = 0; i < nsizes; ++i) {
+    const int64_t lo = (kind == KG_SPQUADFORM && i == 2) ? 0 : 1;  // nnz may be 0
+    if (sizes[i] < lo || sizes[i] >= (int64_t(1) << 31))
+      return fail(KG_ERR_INVALID_ARG, "kg_create: every size must be in [1, 2^31) (nnz in [0, 2^31))");
+  }
   kg_options o;
   kg_options_default(&o);
   if (opt) o = *opt;
@@ -248,6 +250,19 @@ kg_status kg_create(kg_problem** out, int kind, const int64_t* sizes, int nsizes
       }
       rc = tet_setup(p, st);
       break;
+    case KG_SPQUADFORM:
+      if (nsizes != 3 || !data || ndata < 3 || !data[0] || (sizes[2] > 0 && (!data[1] || !data[2]))) {
+        rc = fail(KG_ERR_INVALID_ARG, "kg_create(SPQUADFORM): sizes {m, n, nnz}; data {rowptr, col, val}");
+        break;
+      }
+      p->m = sizes[0];
+      p->n = sizes[1];
+      p->nnz = sizes[2];
+      p->data0 = data[0];
+      p->data1 = data[1];
+      p->data2 = data[2];
+      rc = spq_setup(p, st);
+      break;
     case KG_LAPLACE1D:
       if (nsizes != 1 || !data || ndata < 1 || !data[0]) {
         rc = fail(KG_ERR_INVALID_ARG, "kg_create(LAPLACE1D): sizes {n}; data {b}");
@@ -276,7 +291,10 @@ kg_status kg_create(kg_problem** out, int kind, const int64_t* sizes, int nsizes
     unsigned h = 0;
     cudaError_t e = cudaMemcpy(&h, p->err, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = cuda_fail(e, "kg_create: reading error word");
-    else if (h & ERRBIT_BOUNDS) rc = fail(KG_ERR_BOUNDS, "kg_create: connectivity entry outside [0, N_v)");
+    else if (h & ERRBIT_BOUNDS)
+      rc = fail(KG_ERR_BOUNDS, p->kind == KG_SPQUADFORM
+                                   ? "kg_create: CSR structure invalid (rowptr or a column out of range)"
+                                   : "kg_create: connectivity entry outside [0, N_v)");
   }
   if (rc != KG_OK) {
     std::string keep = t_msg;
@@ -297,6 +315,7 @@ kg_status kg_eval(kg_problem* p, const void* x, void* f, kg_stream s) {
     case KG_QUADFORM: return qf_eval(p, x, f, st);
     case KG_TETENERGY: return tet_eval(p, x, f, false, st);
     case KG_LAPLACE1D: return lap_eval(p, x, f, st);
+    case KG_SPQUADFORM: return spq_eval(p, x, f, st);
   }
   return fail(KG_ERR_STATE, "kg_eval: corrupt handle");
 }
@@ -315,6 +334,7 @@ kg_status kg_grad(kg_problem* p, const void* x, void* f, void* gx, void* gdata, 
       if (gdata) return fail(KG_ERR_UNSUPPORTED, "kg_grad(TETENERGY): no gradient w.r.t. G");
       return tet_grad(p, x, f, gx, seed, accumulate, st);
     case KG_LAPLACE1D: return lap_grad(p, x, f, gx, gdata, seed, accumulate, st);
+    case KG_SPQUADFORM: return spq_grad(p, x, f, gx, gdata, seed, accumulate, st);
   }
   return fail(KG_ERR_STATE, "kg_grad: corrupt handle");
 }

@@ -136,7 +136,7 @@ __global__ void csr_fill_kernel(const int* __restrict__ conn, int64_t n4, int* c
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) {
     const int pos = atomicAdd(cursor + conn[i], 1);
-    inc[pos] = (int)i;  // i = 4 e + k = (e << 2) | k
+    inc[pos] = (int)i;  // tets: i = 4 e + k = (e << 2) | k
   }
 }
 
@@ -220,26 +220,37 @@ kg_status tet_setup(kg_problem* p, cudaStream_t s) {
       return rc;
     if ((rc = ws_alloc(p, (void**)&p->inc, sizeof(int) * (size_t)n4, "CSR incidences")) != KG_OK)
       return rc;
-    int* cursor = nullptr;
-    if ((e = dev_alloc((void**)&cursor, sizeof(int) * (size_t)p->n)) != cudaSuccess)
-      return fail(KG_ERR_OOM, "CSR build cursor allocation failed");
-    bool ok = cudaMemsetAsync(p->rowptr, 0, sizeof(int) * (size_t)(p->n + 1), s) == cudaSuccess;
-    if (ok) {
-      csr_degree_kernel<<<grid_for(n4, 256, 8), 256, 0, s>>>(conn, n4, p->rowptr);
-      csr_scan_kernel<<<1, 1024, 0, s>>>(p->rowptr, (int)p->n);
-      ok = cudaMemcpyAsync(cursor, p->rowptr, sizeof(int) * (size_t)p->n, cudaMemcpyDeviceToDevice,
-                           s) == cudaSuccess;
-    }
-    if (ok) {
-      csr_fill_kernel<<<grid_for(n4, 256, 8), 256, 0, s>>>(conn, n4, cursor, p->inc);
-      csr_sort_kernel<<<grid_for(p->n, 256, 8), 256, 0, s>>>(p->rowptr, (int)p->n, p->inc);
-    }
-    e = cudaGetLastError();
-    cudaError_t e2 = cudaStreamSynchronize(s);
-    cudaFree(cursor);
-    if (!ok || e != cudaSuccess || e2 != cudaSuccess)
-      return cuda_fail(e != cudaSuccess ? e : e2, "CSR build");
+    if ((rc = build_buckets(conn, n4, (int)p->n, p->rowptr, p->inc, s)) != KG_OK) return rc;
   }
+  return KG_OK;
+}
+
+// Buckets of the positions of keys[0..count) by key value (keys in [0, nbins)):
+// binptr[k] .. binptr[k+1] delimit, in perm, the positions i with keys[i] == k,
+// in ascending order.  Device kernels on s (count, scan, fill, per-bucket
+// sort); synchronises s.
+kg_status build_buckets(const int* keys, int64_t count, int nbins, int* binptr, int* perm,
+                        cudaStream_t s) {
+  int* cursor = nullptr;
+  cudaError_t e;
+  if ((e = dev_alloc((void**)&cursor, sizeof(int) * (size_t)std::max(nbins, 1))) != cudaSuccess)
+    return fail(KG_ERR_OOM, "bucket build cursor allocation failed");
+  bool ok = cudaMemsetAsync(binptr, 0, sizeof(int) * (size_t)(nbins + 1), s) == cudaSuccess;
+  if (ok && count > 0) {
+    csr_degree_kernel<<<grid_for(count, 256, 8), 256, 0, s>>>(keys, count, binptr);
+    csr_scan_kernel<<<1, 1024, 0, s>>>(binptr, nbins);
+    ok = cudaMemcpyAsync(cursor, binptr, sizeof(int) * (size_t)nbins, cudaMemcpyDeviceToDevice, s) ==
+         cudaSuccess;
+    if (ok) {
+      csr_fill_kernel<<<grid_for(count, 256, 8), 256, 0, s>>>(keys, count, cursor, perm);
+      csr_sort_kernel<<<grid_for(nbins, 256, 8), 256, 0, s>>>(binptr, nbins, perm);
+    }
+  }
+  e = cudaGetLastError();
+  cudaError_t e2 = cudaStreamSynchronize(s);
+  cudaFree(cursor);
+  if (!ok || e != cudaSuccess || e2 != cudaSuccess)
+    return cuda_fail(e != cudaSuccess ? e : e2, "bucket build");
   return KG_OK;
 }
 
