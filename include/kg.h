@@ -119,9 +119,11 @@ typedef enum {
 /* Forward values for the reverse pass (Sec. 5, taping restriction).
  *   RECOMPUTE  kg_grad reruns the forward pass inside the gradient kernel.
  *   TAPE       kg_create allocates a tape (tet: the per-element adjoint
- *              c_e = G_e^T (2 g_e / (1 + |g_e|^2)), N_e x 4 values);
+ *              c_e = G_e^T (2 g_e / (1 + |g_e|^2)), N_e x 4 values; 1-D:
+ *              the chain's intermediate y = A (3x) - b, n values);
  *              kg_eval_tape fills it and kg_grad_from_tape consumes it.
- *   AUTO       TAPE when the tape fits tape_budget_bytes, else RECOMPUTE. */
+ *   AUTO       tet: TAPE when the tape fits tape_budget_bytes, else
+ *              RECOMPUTE; other kinds: RECOMPUTE. */
 typedef enum { KG_MODE_AUTO = 0, KG_MODE_RECOMPUTE = 1, KG_MODE_TAPE = 2 } kg_mode;
 
 /* FP64 arithmetic.  GB300 has few FP64 units (about 2 FMA per clock per SM),
@@ -197,14 +199,17 @@ kg_status kg_eval(kg_problem *p, const void *x, void *f, kg_stream s);
 kg_status kg_grad(kg_problem *p, const void *x, void *f, void *gx, void *gdata,
                   const void *seed, int accumulate, kg_stream s);
 
-/* TET, TAPE mode: forward pass that also records the per-element adjoint
- * factors c_e (for fbar = 1) in the problem's tape.  f nullable. */
+/* TET and LAPLACE1D, TAPE mode: forward pass that also records, in the
+ * problem's tape, the per-element adjoint factors c_e for fbar = 1 (TET) or the
+ * intermediate y of the chain x -> y -> y^2 -> sum (LAPLACE1D).  f nullable. */
 kg_status kg_eval_tape(kg_problem *p, const void *x, void *f, kg_stream s);
 
-/* TET, TAPE mode: reverse pass from the tape written by the last
- * kg_eval_tape: gx[v] (+)= fbar * sum over incidences (e,k) of v of c_e[k],
- * by atomic scatter or by the CSR gather (the problem's strategy).  Reads no
- * G.  KG_ERR_STATE if no tape was recorded. */
+/* TAPE mode: reverse pass from the tape written by the last kg_eval_tape.
+ * TET: gx[v] (+)= fbar * sum over incidences (e,k) of v of c_e[k], by atomic
+ * scatter or by the CSR gather (the problem's strategy); reads no G.
+ * LAPLACE1D: the reverse chain from y alone, ybar = 2 fbar y and
+ * gx_j (+)= 3 (2 ybar_j - ybar_{j-1} - ybar_{j+1}); reads neither x nor b.
+ * KG_ERR_STATE if no tape was recorded. */
 kg_status kg_grad_from_tape(kg_problem *p, void *gx, const void *seed, int accumulate,
                             kg_stream s);
 

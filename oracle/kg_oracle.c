@@ -241,6 +241,38 @@ int kgo_tet_grad(int64_t ne, int64_t nv, const int32_t *conn, const double *G,
   return 0;
 }
 
+/* Hessian-vector product hv = fbar * (d^2 f / du^2)(u) v: the forward-mode
+ * tangent (direction v) of the reverse pass above (forward over reverse).
+ * Per element, with g = G_e u_e, s = |g|^2, sbar = fbar / (1 + s) and
+ * gbar = 2 sbar g, the tangents are gdot = G_e v_e, sdot = 2 g . gdot,
+ * sbardot = -fbar sdot / (1 + s)^2, gbardot = 2 (sbardot g + sbar gdot), and
+ * the element's contribution G_e^T gbardot is scatter-added like c_e.
+ * hv (nv) is overwritten. */
+int kgo_tet_hvp(int64_t ne, int64_t nv, const int32_t *conn, const double *G, const double *u,
+                const double *v, double fbar, double *hv) {
+  if (ne < 0 || nv < 0 || (nv > 0 && !hv) || (ne > 0 && (!conn || !G || !u || !v))) return -1;
+  if (check_conn(ne, nv, conn)) return -3;
+  nsum *acc = (nsum *)calloc((size_t)(nv > 0 ? nv : 1), sizeof(nsum));
+  if (!acc) return -2;
+  for (int64_t e = 0; e < ne; ++e) {
+    double g[3], gd[3];
+    tet_g(conn, G, u, e, g);
+    tet_g(conn, G, v, e, gd);
+    double s = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+    double sd = 2.0 * (g[0] * gd[0] + g[1] * gd[1] + g[2] * gd[2]);
+    double sbar = fbar / (1.0 + s);
+    double sbard = -fbar * sd / ((1.0 + s) * (1.0 + s));
+    double gbd[3];
+    for (int r = 0; r < 3; ++r) gbd[r] = 2.0 * (sbard * g[r] + sbar * gd[r]);
+    for (int k = 0; k < 4; ++k)
+      nadd(&acc[conn[e * 4 + k]], G[e * 12 + 0 * 4 + k] * gbd[0] + G[e * 12 + 1 * 4 + k] * gbd[1] +
+                                      G[e * 12 + 2 * 4 + k] * gbd[2]);
+  }
+  for (int64_t i = 0; i < nv; ++i) hv[i] = nval(&acc[i]);
+  free(acc);
+  return 0;
+}
+
 /* Gradient descent u <- u - eta * grad f(u), `steps` times, in place.
  * f_hist (steps + 1, nullable) receives f before each step and after the last. */
 int kgo_tet_descent(int64_t ne, int64_t nv, const int32_t *conn, const double *G,
@@ -326,6 +358,33 @@ int kgo_laplace1d_grad(int64_t n, const double *x, const double *b, double fbar,
   }
   if (gx)
     for (int64_t j = 0; j < n; ++j) gx[j] = 3.0 * x3bar[j];
+  free(w);
+  return 0;
+}
+
+/* Hessian-vector product of the 1-D example: the tangent (direction v) of
+ * the forward chain x3 = 3x, y = A x3 - b and of the reverse above; b and x
+ * drop out (f is quadratic in x), ydot = A (3 v), ybardot = 2 fbar ydot and
+ * hv = 3 A^T ybardot with the same boundary guards.  hv (n) is overwritten. */
+int kgo_laplace1d_hvp(int64_t n, const double *v, double fbar, double *hv) {
+  if (n < 0 || (n > 0 && (!v || !hv))) return -1;
+  double *w = (double *)malloc((size_t)(n > 0 ? n : 1) * 2 * sizeof(double));
+  if (!w) return -2;
+  double *yd = w, *x3bd = w + n;
+  for (int64_t j = 0; j < n; ++j) {
+    double t = 2.0 * (3.0 * v[j]);
+    if (j != 0) t -= 3.0 * v[j - 1];
+    if (j != n - 1) t -= 3.0 * v[j + 1];
+    yd[j] = t;
+    x3bd[j] = 0.0;
+  }
+  for (int64_t j = 0; j < n; ++j) {
+    double ybd = 2.0 * yd[j] * fbar;
+    if (j != n - 1) x3bd[j + 1] -= ybd;
+    if (j != 0) x3bd[j - 1] -= ybd;
+    x3bd[j] += 2.0 * ybd;
+  }
+  for (int64_t j = 0; j < n; ++j) hv[j] = 3.0 * x3bd[j];
   free(w);
   return 0;
 }

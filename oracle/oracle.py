@@ -56,6 +56,8 @@ def _load():
                 "kgo_tet_descent": [i64, i64, ip, dp, dp, d, ctypes.c_int, dp],
                 "kgo_spquadform_value": [i64, i64, i64, ip, ip, dp, dp, dp, dp],
                 "kgo_spquadform_grad": [i64, i64, i64, ip, ip, dp, dp, d, dp, dp, dp],
+                "kgo_tet_hvp": [i64, i64, ip, dp, dp, dp, d, dp],
+                "kgo_laplace1d_hvp": [i64, dp, d, dp],
                 "kgo_laplace1d_value": [i64, dp, dp, dp],
                 "kgo_laplace1d_grad": [i64, dp, dp, d, dp, dp, dp],
             }
@@ -158,6 +160,15 @@ def tet_grad(conn, G, u, fbar=1.0):
     return float(f[0]), gu
 
 
+def tet_hvp(conn, G, u, v, fbar=1.0):
+    """fbar * Hessian(u) @ v of the tet energy (forward over reverse)."""
+    conn, G, u, v = _i32(conn), _f64(G), _f64(u), _f64(v)
+    hv = np.empty(u.shape[0])
+    _check(_load().kgo_tet_hvp(conn.shape[0], u.shape[0], _p(conn), _p(G), _p(u), _p(v), float(fbar),
+                               _p(hv)), "tet_hvp")
+    return hv
+
+
 def tet_descent(conn, G, u0, eta, steps):
     """Returns (u after `steps` steps, f history of length steps + 1)."""
     conn, G = _i32(conn), _f64(G)
@@ -185,3 +196,11 @@ def laplace1d_grad(x, b, fbar=1.0):
     _check(_load().kgo_laplace1d_grad(n, _p(x), _p(b), float(fbar), _p(f), _p(gx), _p(gb)),
            "laplace1d_grad")
     return float(f[0]), gx, gb
+
+
+def laplace1d_hvp(v, fbar=1.0):
+    """fbar * Hessian @ v of the 1-D example (independent of x and b)."""
+    v = _f64(v)
+    hv = np.empty(v.shape[0])
+    _check(_load().kgo_laplace1d_hvp(v.shape[0], _p(v), float(fbar), _p(hv)), "laplace1d_hvp")
+    return hv

@@ -76,6 +76,18 @@ class Problem:
         L.kg_grad(self.handle, _dev_tensor(x, self.dtype), f, gx, gdata, seed, int(accumulate), stream)
         return f, gx
 
+    def eval_tape(self, x, f=None, stream=None):
+        """Forward pass that records the problem's tape (TAPE mode)."""
+        f = self._scalar() if f is None else f
+        L.kg_eval_tape(self.handle, _dev_tensor(x, self.dtype), f, stream)
+        return f
+
+    def grad_from_tape(self, gx=None, seed=None, accumulate=False, stream=None):
+        """Reverse pass from the tape of the last eval_tape."""
+        gx = torch.empty(self.nx, dtype=self.dtype, device=self.device) if gx is None else gx
+        L.kg_grad_from_tape(self.handle, gx, seed, int(accumulate), stream)
+        return gx
+
     def grad_host(self, x_host, gx_host, f_host=None, stream=None):
         L.kg_grad_host(self.handle, x_host, f_host, gx_host, stream)
 
@@ -143,16 +155,6 @@ class TetEnergy(Problem):
     @property
     def nx(self):
         return self.nv
-
-    def eval_tape(self, u, f=None, stream=None):
-        f = self._scalar() if f is None else f
-        L.kg_eval_tape(self.handle, _dev_tensor(u, self.dtype), f, stream)
-        return f
-
-    def grad_from_tape(self, gx=None, seed=None, accumulate=False, stream=None):
-        gx = torch.empty(self.nv, dtype=self.dtype, device=self.device) if gx is None else gx
-        L.kg_grad_from_tape(self.handle, gx, seed, int(accumulate), stream)
-        return gx
 
 
 class Laplace1D(Problem):

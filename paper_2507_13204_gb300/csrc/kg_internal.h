@@ -147,6 +147,9 @@ kg_status lap_setup(kg_problem* p, cudaStream_t s);
 kg_status lap_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status lap_grad(kg_problem* p, const void* x, void* f, void* gx, void* gb, const void* seed,
                    int accumulate, cudaStream_t s);
+kg_status lap_eval_tape(kg_problem* p, const void* x, void* f, cudaStream_t s);
+kg_status lap_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,
+                             cudaStream_t s);
 
 // Workspace helper: allocate, record for kg_destroy, count bytes.
 kg_status ws_alloc(kg_problem* p, void** out, size_t bytes, const char* what);

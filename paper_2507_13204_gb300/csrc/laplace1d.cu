@@ -11,6 +11,8 @@
 // stencil's transpose is again a 3-point stencil, so each thread gathers
 // xbar_j = 3 (2 ybar_j - ybar_{j-1} - ybar_{j+1}) with no atomics (the
 // rescheduling and kernel fusion of Sec. 5).
+// KG_MODE_TAPE adds the taped chain: kg_eval_tape records y in the forward
+// kernel, kg_grad_from_tape runs the reverse chain from the tape alone.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -62,6 +64,40 @@ __global__ void __launch_bounds__(256) lap_fused_kernel(const T* __restrict__ x,
   }
   acc = block_sum(acc, scratch);
   finish_sum<T>(acc, fpart, counter, f, 0, scratch);
+}
+
+// ---- TAPE mode: the chain x -> y -> y^2 -> sum with y taped ----------------
+// The forward writes y (the only value the reverse of the chain needs: the
+// reverse of y^2 is 2 y ybar) to a tape of n values allocated once at
+// kg_create (Sec. 5, third restriction); the reverse reads the tape instead of
+// re-running the stencil: xbar_j = 3 (2 ybar_j - ybar_{j-1} - ybar_{j+1}) with
+// ybar = 2 fbar y, b unread.
+template <typename T>
+__global__ void __launch_bounds__(256) lap_tape_kernel(const T* __restrict__ x, const T* __restrict__ b,
+                                                       int n, T* tape, double* fpart,
+                                                       unsigned* counter, T* f) {
+  __shared__ double scratch[32];
+  double acc = 0.0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const T y = lap_y(x, b, j, n);
+    tape[j] = y;
+    acc += (double)(y * y);
+  }
+  acc = block_sum(acc, scratch);
+  finish_sum<T>(acc, fpart, counter, f, 0, scratch);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lap_from_tape_kernel(const T* __restrict__ tape, int n,
+                                                            const T* seed, T* gx, int accumulate) {
+  const T fb2 = T(2) * load_seed(seed);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    T x3b = T(2) * (fb2 * tape[j]);
+    if (j != 0) x3b -= fb2 * tape[j - 1];
+    if (j != n - 1) x3b -= fb2 * tape[j + 1];
+    const T g = T(3) * x3b;
+    gx[j] = accumulate ? gx[j] + g : g;
+  }
 }
 
 // ---- the six kernels of the paper's generated gradient ------------------
@@ -130,10 +166,14 @@ kg_status lap_setup(kg_problem* p, cudaStream_t s) {
   if (p->strategy == KG_STRATEGY_AUTO) p->strategy = KG_STRATEGY_FUSED;
   if (p->strategy != KG_STRATEGY_FUSED && p->strategy != KG_STRATEGY_ATOMIC)
     return fail(KG_ERR_UNSUPPORTED, "LAPLACE1D: strategy must be FUSED or ATOMIC");
-  p->mode = KG_MODE_RECOMPUTE;
+  // TAPE on request only: the fused recompute is one pass over x and b either way
+  p->mode = p->mode == KG_MODE_TAPE ? KG_MODE_TAPE : KG_MODE_RECOMPUTE;
   if (p->arith == KG_ARITH_AUTO) p->arith = KG_ARITH_NATIVE;
   kg_status rc = ws_common(p, lap_grid(p->n), s);
   if (rc != KG_OK) return rc;
+  if (p->mode == KG_MODE_TAPE &&
+      (rc = ws_alloc(p, &p->tape, p->esize * (size_t)p->n, "1-D tape y")) != KG_OK)
+    return rc;
   if (p->strategy == KG_STRATEGY_ATOMIC) {
     // x3, y, y2 (forward "views") and their shadows y2bar, ybar, x3bar
     rc = ws_alloc(p, &p->y, p->esize * 6 * (size_t)p->n, "1-D views and shadows");
@@ -196,6 +236,46 @@ kg_status lap_grad(kg_problem* p, const void* x, void* f, void* gx, void* gb, co
                    int accumulate, cudaStream_t s) {
   return p->dtype == KG_F64 ? lap_grad_t<double>(p, x, f, gx, gb, seed, accumulate, s)
                             : lap_grad_t<float>(p, x, f, gx, gb, seed, accumulate, s);
+}
+
+template <typename T>
+static kg_status lap_eval_tape_t(kg_problem* p, const void* x, void* f, cudaStream_t s) {
+  const int n = (int)p->n;
+  prof_begin(s, "lap_tape_kernel");
+  lap_tape_kernel<T><<<lap_grid(n), 256, 0, s>>>(static_cast<const T*>(x),
+                                                 static_cast<const T*>(p->data0), n,
+                                                 static_cast<T*>(p->tape), p->fpart, p->counter,
+                                                 static_cast<T*>(f));
+  prof_end(s);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "1-D taping forward kernel");
+  p->tape_valid = true;
+  return KG_OK;
+}
+
+template <typename T>
+static kg_status lap_grad_from_tape_t(kg_problem* p, void* gx, const void* seed, int accumulate,
+                                      cudaStream_t s) {
+  const int n = (int)p->n;
+  prof_begin(s, "lap_from_tape_kernel");
+  lap_from_tape_kernel<T><<<lap_grid(n), 256, 0, s>>>(static_cast<const T*>(p->tape), n,
+                                                      static_cast<const T*>(seed),
+                                                      static_cast<T*>(gx), accumulate);
+  prof_end(s);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KG_OK : cuda_fail(e, "1-D reverse from tape");
+}
+
+kg_status lap_eval_tape(kg_problem* p, const void* x, void* f, cudaStream_t s) {
+  return p->dtype == KG_F64 ? lap_eval_tape_t<double>(p, x, f, s) : lap_eval_tape_t<float>(p, x, f, s);
+}
+
+kg_status lap_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,
+                             cudaStream_t s) {
+  return p->dtype == KG_F64 ? lap_grad_from_tape_t<double>(p, gx, seed, accumulate, s)
+                            : lap_grad_from_tape_t<float>(p, gx, seed, accumulate, s);
 }
 
 }  // namespace kg

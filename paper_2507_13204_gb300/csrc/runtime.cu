@@ -342,10 +342,12 @@ kg_status kg_grad(kg_problem* p, const void* x, void* f, void* gx, void* gdata, 
 kg_status kg_eval_tape(kg_problem* p, const void* x, void* f, kg_stream s) {
   reset_launch_count();
   if (!p || !x) return fail(KG_ERR_INVALID_ARG, "kg_eval_tape: NULL argument");
-  if (p->kind != KG_TETENERGY) return fail(KG_ERR_UNSUPPORTED, "kg_eval_tape: TETENERGY only");
+  if (p->kind != KG_TETENERGY && p->kind != KG_LAPLACE1D)
+    return fail(KG_ERR_UNSUPPORTED, "kg_eval_tape: TETENERGY and LAPLACE1D only");
   if (!p->tape) return fail(KG_ERR_STATE, "kg_eval_tape: problem was not created in TAPE mode");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
   p->last_stream = st;
+  if (p->kind == KG_LAPLACE1D) return lap_eval_tape(p, x, f, st);
   return tet_eval(p, x, f, true, st);
 }
 
@@ -353,13 +355,15 @@ kg_status kg_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accum
                             kg_stream s) {
   reset_launch_count();
   if (!p || !gx) return fail(KG_ERR_INVALID_ARG, "kg_grad_from_tape: NULL argument");
-  if (p->kind != KG_TETENERGY) return fail(KG_ERR_UNSUPPORTED, "kg_grad_from_tape: TETENERGY only");
+  if (p->kind != KG_TETENERGY && p->kind != KG_LAPLACE1D)
+    return fail(KG_ERR_UNSUPPORTED, "kg_grad_from_tape: TETENERGY and LAPLACE1D only");
   if (!p->tape || !p->tape_valid)
     return fail(KG_ERR_STATE, "kg_grad_from_tape: no tape recorded (call kg_eval_tape first)");
   if (accumulate != 0 && accumulate != 1)
     return fail(KG_ERR_INVALID_ARG, "kg_grad_from_tape: accumulate must be 0 or 1");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
   p->last_stream = st;
+  if (p->kind == KG_LAPLACE1D) return lap_grad_from_tape(p, gx, seed, accumulate, st);
   return tet_grad_from_tape(p, gx, seed, accumulate, st);
 }
 

@@ -70,3 +70,34 @@ def test_f32_and_accumulate(api):
         p.sync()
         assert rel_scalar(f.item(), f_ref) <= TOL["f32"]
         assert rel_l2(gx.cpu().numpy() - 1.0, gx_ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 4096, 100003])
+def test_tape_mode_chain_from_tape(api, n):
+    # the forward records y; the reverse chain runs from the tape alone (x and b are not read:
+    # they are overwritten between the two calls)
+    from paper_2507_13204_gb300 import _lib as L
+    x, b = W.laplace1d_inputs(n, seed=n)
+    f_ref, gx_ref, _ = O.laplace1d_grad(x, b, fbar=-0.5)
+    bt = torch.tensor(b, device="cuda")
+    p = api.Laplace1D(bt, mode="tape")
+    assert p.config[1] == "tape"
+    xt = torch.tensor(x, device="cuda")
+    with pytest.raises(L.KGError) as ei:
+        p.grad_from_tape()
+    assert ei.value.status == L.KG_ERR_STATE
+    f = p.eval_tape(xt)
+    xt.fill_(123.0)
+    bt.fill_(-7.0)
+    seed = torch.tensor(-0.5, dtype=torch.float64, device="cuda")
+    g = torch.full((n,), 0.25, dtype=torch.float64, device="cuda")
+    p.grad_from_tape(gx=g, seed=seed, accumulate=True)
+    p.sync()
+    assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+    assert rel_l2(g.cpu().numpy() - 0.25, gx_ref) <= TOL["f64"]
+    # the default mode has no tape
+    q = api.Laplace1D(torch.tensor(b, device="cuda"))
+    assert q.config[1] == "recompute"
+    with pytest.raises(L.KGError) as ei:
+        q.eval_tape(torch.tensor(x, device="cuda"))
+    assert ei.value.status == L.KG_ERR_STATE

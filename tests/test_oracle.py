@@ -428,6 +428,54 @@ def test_laplace1d_dual_numbers():
         assert f_dual(list(x), seed(b, j)).d == pytest.approx(gb[j], rel=1e-13, abs=1e-14)
 
 
+# ------------------------------------------------------------------ Hessian-vector products
+def test_tet_hvp_central_difference_of_gradient():
+    mesh = W.tet_mesh(3, 2, 2, jitter_seed=2, perm_seed=5)
+    rng = np.random.default_rng(31)
+    u, v = rng.uniform(-1, 1, mesh.nv), rng.uniform(-1, 1, mesh.nv)
+    hv = O.tet_hvp(mesh.conn, mesh.G, u, v, fbar=0.7)
+    h = 1e-5
+    fd = (O.tet_grad(mesh.conn, mesh.G, u + h * v, fbar=0.7)[1]
+          - O.tet_grad(mesh.conn, mesh.G, u - h * v, fbar=0.7)[1]) / (2 * h)
+    assert rel(hv, fd) < 1e-8
+
+
+def test_tet_hvp_is_symmetric():
+    mesh = W.tet_mesh(3, jitter_seed=4, perm_seed=2)
+    rng = np.random.default_rng(32)
+    u, v, w = (rng.uniform(-1, 1, mesh.nv) for _ in range(3))
+    a = w @ O.tet_hvp(mesh.conn, mesh.G, u, v)
+    b = v @ O.tet_hvp(mesh.conn, mesh.G, u, w)
+    assert a == pytest.approx(b, rel=1e-12)
+
+
+def test_tet_hvp_at_zero_is_the_stacked_quadratic_form():
+    # at u = 0 every element contributes fbar * 2 G_e^T G_e: the Hessian of
+    # fbar * ||B v||^2 with B the 3 N_e x N_v matrix whose rows are G_e placed at conn[e]
+    mesh = W.tet_mesh(2, jitter_seed=3, perm_seed=7)
+    B = np.zeros((3 * mesh.ne, mesh.nv))
+    for e in range(mesh.ne):
+        for r in range(3):
+            for k in range(4):
+                B[3 * e + r, mesh.conn[e, k]] += mesh.G[e, 4 * r + k]
+    v = np.random.default_rng(33).uniform(-1, 1, mesh.nv)
+    hv = O.tet_hvp(mesh.conn, mesh.G, np.zeros(mesh.nv), v, fbar=1.5)
+    assert rel(hv, O.quadform_grad(B, v, fbar=1.5)[1]) < 1e-13
+
+
+def test_laplace1d_hvp_linearity_and_difference():
+    # f is quadratic in x: H v = grad(v, b) - grad(0, b) for any b, and H is symmetric
+    for n in (1, 2, 9, 50):
+        x, b = W.laplace1d_inputs(n, seed=n)
+        v = np.random.default_rng(n).uniform(-1, 1, n)
+        hv = O.laplace1d_hvp(v, fbar=0.5)
+        g1 = O.laplace1d_grad(v, b, fbar=0.5)[1]
+        g0 = O.laplace1d_grad(np.zeros(n), b, fbar=0.5)[1]
+        assert rel(hv, g1 - g0) < 1e-13
+        w = np.random.default_rng(n + 1).uniform(-1, 1, n)
+        assert w @ hv == pytest.approx(v @ O.laplace1d_hvp(w, fbar=0.5), rel=1e-12)
+
+
 # ------------------------------------------------------------------ mutation check
 def test_pins_catch_planted_mistakes(tmp_path):
     """Build oracle copies with one plausible mistake each and check a pin fails."""
@@ -444,6 +492,8 @@ def test_pins_catch_planted_mistakes(tmp_path):
                               "if (j + 1 < n) x3bar[j + 1] += ybar;"),
         "sp_scatter_to_row": ("nadd(&acc[col[p]], val[p] * ybar);", "nadd(&acc[i % n], val[p] * ybar);"),
         "sp_gather_first_col": ("nadd(&yi, val[p] * x[col[p]]);", "nadd(&yi, val[p] * x[col[rowptr[i]]]);"),
+        "hvp_dropped_curvature": ("double sbard = -fbar * sd / ((1.0 + s) * (1.0 + s));",
+                                  "double sbard = 0.0;"),
     }
     for name, (old, new) in mutants.items():
         assert old in src, name
@@ -470,6 +520,17 @@ def test_pins_catch_planted_mistakes(tmp_path):
                                     p(f), p(gx), None)
             D = A.dense()
             caught = rel(gx, 2 * D.T @ (D @ x)) > 1e-6
+        elif name.startswith("hvp"):
+            mesh = W.tet_mesh(2, jitter_seed=3, perm_seed=1)
+            rng = np.random.default_rng(34)
+            u, v = rng.uniform(-1, 1, mesh.nv), rng.uniform(-1, 1, mesh.nv)
+            hv = np.empty(mesh.nv)
+            conn, G = np.ascontiguousarray(mesh.conn), np.ascontiguousarray(mesh.G)
+            lib.kgo_tet_hvp(ctypes.c_int64(mesh.ne), ctypes.c_int64(mesh.nv), p(conn), p(G), p(u), p(v),
+                            ctypes.c_double(1.0), p(hv))
+            h = 1e-5
+            fd = (O.tet_grad(conn, G, u + h * v)[1] - O.tet_grad(conn, G, u - h * v)[1]) / (2 * h)
+            caught = rel(hv, fd) > 1e-6
         elif name.startswith("tet"):
             conn, G = _ref_tet()
             u = np.array([0.3, -0.7, 0.25, 0.9])
