@@ -27,6 +27,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -354,6 +356,63 @@ class TetWL(Workload):
         return b / 1e9 / dt, f"{reps} x value+grad of the first {ne} tets (oracle, 1 thread)"
 
 
+class HvpWL(TetWL):
+    """Hessian-vector product of the tet energy (forward mode over the reverse pass) on the
+    100^3 x 6 mesh; the comparison line (ms_eval, ratio) is the value+grad of the same mesh."""
+
+    def setup(self, dev):
+        import torch
+        super().setup(dev)
+        td = self.u.dtype
+        v = np.random.default_rng(43).uniform(-1.0, 1.0, self.nv)
+        self.v = torch.tensor(v, dtype=td, device=dev)
+        self.hv = torch.empty(self.nv, dtype=td, device=dev)
+        self.v_pin = torch.tensor(v, dtype=td).pin_memory()
+        self.stream = torch.cuda.current_stream()
+
+    def step(self):
+        self.p.hvp(self.u, self.v, hv=self.hv)
+
+    def eval_step(self):  # the comparison: value+grad
+        self.p.grad(self.u, gx=self.gu, f=self.f)
+
+    def e2e_step(self):
+        self.u.copy_(self.x_pin, non_blocking=True)
+        self.v.copy_(self.v_pin, non_blocking=True)
+        self.p.hvp(self.u, self.v, hv=self.hv)
+        self.g_pin.copy_(self.hv, non_blocking=True)
+        self.stream.synchronize()
+
+    @property
+    def grad_bytes(self):  # conn + G streamed, u and v read, hv written
+        return self.ne * (16 + 12 * self.es) + 3 * self.nv * self.es
+
+    def h2d_d2h(self):
+        return 2 * self.es * self.nv, self.es * self.nv
+
+    def config(self):
+        c = super().config()
+        c["workload"] = c["workload"].replace("value+grad wrt u", "Hessian-vector product H(u) v")
+        c["comparison"] = "ms_eval / grad_over_eval_ratio here are the value+grad of the same mesh"
+        return c
+
+    def oracle_sample(self, budget_s=10.0):
+        from oracle import oracle as O
+        ne = min(self.ne, 1_000_000)
+        conn, G = self.mesh.conn[:ne], self.mesh.G[:ne]
+        v = np.random.default_rng(43).uniform(-1.0, 1.0, self.nv)
+        t0 = time.perf_counter()
+        reps = 0
+        while True:
+            O.tet_hvp(conn, G, self.u_host, v)
+            reps += 1
+            if time.perf_counter() - t0 >= budget_s or reps >= 20:
+                break
+        dt = time.perf_counter() - t0
+        b = reps * (ne * (16 + 12 * self.es) + 3 * self.nv * self.es)
+        return b / 1e9 / dt, f"{reps} x Hessian-vector product on the first {ne} tets (oracle, 1 thread)"
+
+
 class LaplaceWL(Workload):
     """The paper's E1 example at n = 10000 (data 80 KB: launch-bound, like the paper)."""
 
@@ -630,6 +689,10 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
         return TetWL(size or 100, "f32", strategy=strategy or "auto")
     if name == "tetcsr":
         return TetWL(size or 100, "f64", strategy="csr", arith=arith)
+    if name == "hvp":
+        return HvpWL(size or 100, "f64", strategy=strategy or "auto", arith=arith)
+    if name == "hvp32":
+        return HvpWL(size or 100, "f32", strategy=strategy or "auto")
     if name == "sparse":
         return SparseWL(size or (1 << 20), "f64", strategy=strategy or "auto")
     if name == "sparse32":
@@ -966,6 +1029,15 @@ def run_reference(args, rank, world):
         unit_bytes = wl.es * (rows * wl.n + 2 * wl.n)
         fn = lambda: O.quadform_grad(A, x)
         sample = f"value+grad of the first {rows} rows of the {wl.n}x{wl.n} problem per step"
+        to_value = lambda s: unit_bytes / 1e9 / s
+    elif isinstance(wl, HvpWL):
+        mesh, u = W.tet_inputs(wl.a)
+        ne = 500_000
+        conn, G = mesh.conn[:ne], mesh.G[:ne]
+        v = np.random.default_rng(43).uniform(-1.0, 1.0, mesh.nv)
+        unit_bytes = ne * (16 + 12 * wl.es) + 3 * mesh.nv * wl.es
+        fn = lambda: O.tet_hvp(conn, G, u, v)
+        sample = f"Hessian-vector product on the first {ne} tets of the {wl.a}^3 mesh per step"
         to_value = lambda s: unit_bytes / 1e9 / s
     elif isinstance(wl, TetWL):
         mesh, u = W.tet_inputs(wl.a)

@@ -213,6 +213,17 @@ kg_status kg_eval_tape(kg_problem *p, const void *x, void *f, kg_stream s);
 kg_status kg_grad_from_tape(kg_problem *p, void *gx, const void *seed, int accumulate,
                             kg_stream s);
 
+/* Hessian-vector product (forward mode over the reverse pass; the paper's
+ * Sec. 5 lists forward mode as future work): hv (+)= fbar * H(x) v with H the
+ * Hessian of f w.r.t. x.  TETENERGY: per element the tangent of the reverse
+ * pass in direction v, scatter-added like the gradient (the problem's
+ * scatter strategy; CSR uses atomics here); x is needed.  QUADFORM and
+ * SPQUADFORM: f is a homogeneous quadratic, so H v is the gradient at v (x
+ * unused, may be NULL).  LAPLACE1D: 18 fbar A^T A v (x unused).  v and hv:
+ * length n or N_v; seed nullable (fbar = 1).  Allocates nothing. */
+kg_status kg_hvp(kg_problem *p, const void *x, const void *v, void *hv, const void *seed,
+                 int accumulate, kg_stream s);
+
 /* End-to-end variant of kg_grad on HOST buffers: copies x (pageable or
  * pinned host memory) to the device, runs kg_grad with seed 1 on `s`, copies
  * f and gx back and synchronises `s`.  f_host nullable. */

@@ -30,7 +30,7 @@ EXPORTS = ["kg_options_default", "kg_create", "kg_eval", "kg_grad", "kg_eval_tap
            "kg_grad_from_tape", "kg_grad_host", "kg_batch_create", "kg_grad_batched",
            "kg_grad_batched_loop", "kg_batch_get_config", "kg_sync", "kg_batch_sync", "kg_last_error",
            "kg_get_config", "kg_workspace_bytes", "kg_last_launch_count", "kg_profile_enable", "kg_profile_read",
-           "kg_quadform_grad_noalloc", "kg_destroy", "kg_batch_destroy"]
+           "kg_quadform_grad_noalloc", "kg_hvp", "kg_destroy", "kg_batch_destroy"]
 
 
 class kg_options(ctypes.Structure):
@@ -71,6 +71,7 @@ def lib():
                 "kg_grad": (st, [vp, vp, vp, vp, vp, vp, i, vp]),
                 "kg_eval_tape": (st, [vp, vp, vp, vp]),
                 "kg_grad_from_tape": (st, [vp, vp, vp, i, vp]),
+                "kg_hvp": (st, [vp, vp, vp, vp, vp, i, vp]),
                 "kg_grad_host": (st, [vp, vp, vp, vp, vp]),
                 "kg_batch_create": (st, [ctypes.POINTER(vp), vpp, i, optp, vp]),
                 "kg_grad_batched": (st, [vp, vpp, vpp, vpp, vp]),
@@ -152,6 +153,11 @@ def kg_eval(h, x, f, stream=None):
 def kg_grad(h, x, f, gx, gdata=None, seed=None, accumulate=0, stream=None):
     check(lib().kg_grad(h, ptr(x), ptr(f), ptr(gx), ptr(gdata), ptr(seed), int(accumulate),
                         stream_handle(stream)), "kg_grad")
+
+
+def kg_hvp(h, x, v, hv, seed=None, accumulate=0, stream=None):
+    check(lib().kg_hvp(h, ptr(x), ptr(v), ptr(hv), ptr(seed), int(accumulate), stream_handle(stream)),
+          "kg_hvp")
 
 
 def kg_eval_tape(h, x, f=None, stream=None):

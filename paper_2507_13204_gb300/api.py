@@ -76,6 +76,13 @@ class Problem:
         L.kg_grad(self.handle, _dev_tensor(x, self.dtype), f, gx, gdata, seed, int(accumulate), stream)
         return f, gx
 
+    def hvp(self, x, v, hv=None, seed=None, accumulate=False, stream=None):
+        """Hessian-vector product fbar * H(x) v (x may be None for the quadratic kinds)."""
+        hv = torch.empty(self.nx, dtype=self.dtype, device=self.device) if hv is None else hv
+        L.kg_hvp(self.handle, None if x is None else _dev_tensor(x, self.dtype),
+                 _dev_tensor(v, self.dtype), hv, seed, int(accumulate), stream)
+        return hv
+
     def eval_tape(self, x, f=None, stream=None):
         """Forward pass that records the problem's tape (TAPE mode)."""
         f = self._scalar() if f is None else f

@@ -120,11 +120,12 @@ kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const vo
 kg_status logtab_for_device(const float4** out);
 LogConsts log_consts();
 
-// staged tet kernels (tet_pair.cu); mode 0 eval, 1 grad (atomic scatter), 2 tape
+// staged tet kernels (tet_pair.cu); mode 0 eval, 1 grad, 2 tape, 3 Hessian-vector
+// product in direction v
 int tet_staged_grid(const kg_problem* p);
 kg_status tet_staged_setup(kg_problem* p);
 kg_status tet_staged(kg_problem* p, int mode, const void* x, void* f, void* gx, const void* seed,
-                     cudaStream_t s);
+                     cudaStream_t s, const void* v = nullptr);
 
 kg_status tet_setup(kg_problem* p, cudaStream_t s);
 kg_status tet_eval(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s);
@@ -132,6 +133,8 @@ kg_status tet_grad(kg_problem* p, const void* x, void* f, void* gx, const void* 
                    int accumulate, cudaStream_t s);
 kg_status tet_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,
                              cudaStream_t s);
+kg_status tet_hvp(kg_problem* p, const void* x, const void* v, void* hv, const void* seed,
+                  int accumulate, cudaStream_t s);
 
 // Buckets of positions by key (transposed index lists; tet.cu), synchronises s.
 kg_status build_buckets(const int* keys, int64_t count, int nbins, int* binptr, int* perm,
@@ -148,6 +151,8 @@ kg_status lap_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status lap_grad(kg_problem* p, const void* x, void* f, void* gx, void* gb, const void* seed,
                    int accumulate, cudaStream_t s);
 kg_status lap_eval_tape(kg_problem* p, const void* x, void* f, cudaStream_t s);
+kg_status lap_hvp(kg_problem* p, const void* v, void* hv, const void* seed, int accumulate,
+                  cudaStream_t s);
 kg_status lap_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,
                              cudaStream_t s);
 

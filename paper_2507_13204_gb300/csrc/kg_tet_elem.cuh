@@ -18,7 +18,7 @@
 
 namespace kg {
 
-enum { TS_EVAL = 0, TS_GRAD = 1, TS_TAPE = 2 };
+enum { TS_EVAL = 0, TS_GRAD = 1, TS_TAPE = 2, TS_HVP = 3 };
 
 __device__ __forceinline__ Acc shfl_xor_acc2(Acc a, int o) {
   Acc b;
@@ -244,6 +244,106 @@ __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict
       reinterpret_cast<double2*>(tape_e)[0] = make_double2(cd[0], cd[1]);
       reinterpret_cast<double2*>(tape_e)[1] = make_double2(cd[2], cd[3]);
     }
+  }
+}
+
+// Hessian-vector product of one element (forward-mode tangent, direction v,
+// of the reverse pass): with g = G u_e, gd = G v_e, s = |g|^2, t = 1 + s,
+// w = 2 fbar / t, sd = 2 g . gd and wd = -w sd / t, the element adds
+// G^T (wd g + w gd) at its four vertices.  Native arithmetic.
+template <typename T, typename Sink>
+__device__ __forceinline__ void elem_native_hvp(const int4 c, const T* __restrict__ Gs,
+                                                const T* __restrict__ u, const T* __restrict__ v,
+                                                T fb, const Sink& gu) {
+  T G[12];
+#pragma unroll
+  for (int i = 0; i < 12; ++i) G[i] = Gs[i];
+  const T u0 = __ldg(u + c.x), u1 = __ldg(u + c.y), u2 = __ldg(u + c.z), u3 = __ldg(u + c.w);
+  const T v0 = __ldg(v + c.x), v1 = __ldg(v + c.y), v2 = __ldg(v + c.z), v3 = __ldg(v + c.w);
+  T g[3], gd[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    g[r] = G[4 * r] * u0 + G[4 * r + 1] * u1 + G[4 * r + 2] * u2 + G[4 * r + 3] * u3;
+    gd[r] = G[4 * r] * v0 + G[4 * r + 1] * v1 + G[4 * r + 2] * v2 + G[4 * r + 3] * v3;
+  }
+  const T s = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+  const T sd = T(2) * (g[0] * gd[0] + g[1] * gd[1] + g[2] * gd[2]);
+  const T t = T(1) + s;
+  const T w = T(2) * fb / t;
+  const T wd = -w * sd / t;
+  T h[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) h[r] = wd * g[r] + w * gd[r];
+  gu(0, c.x, G[0] * h[0] + G[4] * h[1] + G[8] * h[2]);
+  gu(1, c.y, G[1] * h[0] + G[5] * h[1] + G[9] * h[2]);
+  gu(2, c.z, G[2] * h[0] + G[6] * h[1] + G[10] * h[2]);
+  gu(3, c.w, G[3] * h[0] + G[7] * h[1] + G[11] * h[2]);
+}
+
+// The same in float-pair arithmetic (FP64 data); fb2 = 2 fbar as a pair.
+template <typename Sink, bool PREP = false>
+__device__ __forceinline__ void elem_pair_hvp(const int4 c, const double* __restrict__ Gs,
+                                              const double* __restrict__ u,
+                                              const double* __restrict__ v, Pair fb2,
+                                              const Sink& gu, bool& bad) {
+  Pair G[12];
+#pragma unroll
+  for (int i = 0; i < 12; i += 2) {
+    if constexpr (PREP) {
+      const float4 q = *reinterpret_cast<const float4*>(Gs + i);
+      G[i] = Pair{q.x, q.y};
+      G[i + 1] = Pair{q.z, q.w};
+    } else {
+      const double2 q = *reinterpret_cast<const double2*>(Gs + i);
+      G[i] = split_f64(q.x);
+      G[i + 1] = split_f64(q.y);
+    }
+  }
+  const int idx[4] = {c.x, c.y, c.z, c.w};
+  Pair U[4], V[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double uk = __ldg(u + idx[k]), vk = __ldg(v + idx[k]);
+    bad |= !pair_in_range(uk) || !pair_in_range(vk);
+    U[k] = split_f64(uk);
+    V[k] = split_f64(vk);
+  }
+  Pair g[3], gd[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    Acc a = acc_zero(), b = acc_zero();
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, U[k].h, U[k].l);
+      acc_fma(b, G[4 * r + k].h, G[4 * r + k].l, V[k].h, V[k].l);
+    }
+    g[r] = acc_pair(a);
+    gd[r] = acc_pair(b);
+  }
+  Acc sa = acc_zero(), sda = acc_zero();
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    acc_fma(sa, g[r].h, g[r].l, g[r].h, g[r].l);
+    acc_fma(sda, g[r].h, g[r].l, gd[r].h, gd[r].l);
+  }
+  const Pair s = acc_pair(sa);
+  Pair sd = acc_pair(sda);
+  sd.h *= 2.0f;  // exact
+  sd.l *= 2.0f;
+  const Pair rt = pair_recip(pair_add(Pair{1.0f, 0.0f}, s));
+  const Pair w = pair_mul(fb2, rt);
+  Pair wd = pair_mul(pair_mul(w, sd), rt);
+  wd.h = -wd.h;
+  wd.l = -wd.l;
+  Pair h[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) h[r] = pair_add(pair_mul(wd, g[r]), pair_mul(w, gd[r]));
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    Acc a = acc_zero();
+#pragma unroll
+    for (int r = 0; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, h[r].h, h[r].l);
+    sink_pair(gu, k, idx[k], acc_pair(a));
   }
 }
 

@@ -100,6 +100,30 @@ __global__ void __launch_bounds__(256) lap_from_tape_kernel(const T* __restrict_
   }
 }
 
+// Hessian-vector product: the tangent (direction v) of the fused value-and-
+// gradient; f is quadratic in x, so x and b drop out: ydot_j = (A (3v))_j and
+// hv_j = 3 (2 ybd_j - ybd_{j-1} - ybd_{j+1}) with ybd = 2 fbar ydot.
+template <typename T>
+__device__ __forceinline__ T lap_ydot(const T* __restrict__ v, int j, int n) {
+  T t = T(2) * (T(3) * v[j]);
+  if (j != 0) t -= T(3) * v[j - 1];
+  if (j != n - 1) t -= T(3) * v[j + 1];
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) lap_hvp_kernel(const T* __restrict__ v, int n, const T* seed,
+                                                      T* hv, int accumulate) {
+  const T fb2 = T(2) * load_seed(seed);
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    T x3b = T(2) * (fb2 * lap_ydot(v, j, n));
+    if (j != 0) x3b -= fb2 * lap_ydot(v, j - 1, n);
+    if (j != n - 1) x3b -= fb2 * lap_ydot(v, j + 1, n);
+    const T g = T(3) * x3b;
+    hv[j] = accumulate ? hv[j] + g : g;
+  }
+}
+
 // ---- the six kernels of the paper's generated gradient ------------------
 template <typename T>
 __global__ void lap_k1_scale(const T* x, T* x3, int n) {
@@ -276,6 +300,26 @@ kg_status lap_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accu
                              cudaStream_t s) {
   return p->dtype == KG_F64 ? lap_grad_from_tape_t<double>(p, gx, seed, accumulate, s)
                             : lap_grad_from_tape_t<float>(p, gx, seed, accumulate, s);
+}
+
+template <typename T>
+static kg_status lap_hvp_t(kg_problem* p, const void* v, void* hv, const void* seed, int accumulate,
+                           cudaStream_t s) {
+  const int n = (int)p->n;
+  prof_begin(s, "lap_hvp_kernel");
+  lap_hvp_kernel<T><<<lap_grid(n), 256, 0, s>>>(static_cast<const T*>(v), n,
+                                                static_cast<const T*>(seed), static_cast<T*>(hv),
+                                                accumulate);
+  prof_end(s);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KG_OK : cuda_fail(e, "1-D Hessian-vector kernel");
+}
+
+kg_status lap_hvp(kg_problem* p, const void* v, void* hv, const void* seed, int accumulate,
+                  cudaStream_t s) {
+  return p->dtype == KG_F64 ? lap_hvp_t<double>(p, v, hv, seed, accumulate, s)
+                            : lap_hvp_t<float>(p, v, hv, seed, accumulate, s);
 }
 
 }  // namespace kg

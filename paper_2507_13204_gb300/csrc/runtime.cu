@@ -351,6 +351,26 @@ kg_status kg_eval_tape(kg_problem* p, const void* x, void* f, kg_stream s) {
   return tet_eval(p, x, f, true, st);
 }
 
+kg_status kg_hvp(kg_problem* p, const void* x, const void* v, void* hv, const void* seed,
+                 int accumulate, kg_stream s) {
+  reset_launch_count();
+  if (!p || !v || !hv) return fail(KG_ERR_INVALID_ARG, "kg_hvp: NULL argument");
+  if (accumulate != 0 && accumulate != 1)
+    return fail(KG_ERR_INVALID_ARG, "kg_hvp: accumulate must be 0 or 1");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  p->last_stream = st;
+  switch (p->kind) {
+    // ||A x||^2 is a homogeneous quadratic: its Hessian times v is its gradient at v
+    case KG_QUADFORM: return qf_grad(p, v, p->fdev, hv, nullptr, seed, accumulate, st);
+    case KG_SPQUADFORM: return spq_grad(p, v, p->fdev, hv, nullptr, seed, accumulate, st);
+    case KG_LAPLACE1D: return lap_hvp(p, v, hv, seed, accumulate, st);
+    case KG_TETENERGY:
+      if (!x) return fail(KG_ERR_INVALID_ARG, "kg_hvp: x is NULL");
+      return tet_hvp(p, x, v, hv, seed, accumulate, st);
+  }
+  return fail(KG_ERR_INVALID_ARG, "kg_hvp: bad problem");
+}
+
 kg_status kg_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,
                             kg_stream s) {
   reset_launch_count();

@@ -315,6 +315,16 @@ kg_status tet_grad(kg_problem* p, const void* x, void* f, void* gx, const void* 
                             : tet_grad_t<float>(p, x, f, gx, seed, accumulate, s);
 }
 
+kg_status tet_hvp(kg_problem* p, const void* x, const void* v, void* hv, const void* seed,
+                  int accumulate, cudaStream_t s) {
+  if (!accumulate) {
+    cudaError_t e = cudaMemsetAsync(hv, 0, p->esize * (size_t)p->n, s);
+    if (e != cudaSuccess) return cuda_fail(e, "zero hv");
+    count_launch();
+  }
+  return tet_staged(p, 3, x, nullptr, hv, seed, s, v);
+}
+
 kg_status tet_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,
                              cudaStream_t s) {
   return p->dtype == KG_F64 ? tet_scatter_t<double>(p, gx, seed, accumulate, s)

@@ -60,6 +60,7 @@ struct TsArgs {
   const int4* conn;
   const T* G;  // N_e x 12 values, or (PREP) N_e x 12 float pairs in the same bytes
   const T* u;
+  const T* v;  // TS_HVP: the direction
   int64_t ne;
   int nv;
   const T* seed;
@@ -80,7 +81,8 @@ enum { SC_ATOMIC = 0, SC_SHARED = 1, SC_WARP = 2 };
 template <typename T, bool PAIR, int MODE, int SCAT, bool PREP>
 __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
   constexpr bool SHARED = SCAT == SC_SHARED;
-  constexpr bool WARPC = SCAT == SC_WARP && MODE == TS_GRAD;
+  constexpr bool REV = MODE == TS_GRAD || MODE == TS_HVP;  // scatters into gu
+  constexpr bool WARPC = SCAT == SC_WARP && REV;
   constexpr int TS_STAGES = ts_stages<T, MODE>();
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr uint32_t kConnBytes = TS_THREADS * 16u;
@@ -140,10 +142,10 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
   T facc_n = T(0);
   Acc facc_p = acc_zero();
   bool bad = false;
-  const T fb = MODE == TS_GRAD ? load_seed(a.seed) : T(1);
+  const T fb = REV ? load_seed(a.seed) : T(1);
   Pair fb2{2.0f, 0.0f};
   if constexpr (PAIR) {
-    if (MODE == TS_GRAD) {
+    if (REV) {
       bad |= !pair_in_range(2.0 * (double)fb);
       fb2 = split_f64(2.0 * (double)fb);
     }
@@ -176,7 +178,14 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
       if (inb) {
         const int tb = (int)(i & 1) * kSlots;
         auto run = [&](const auto& sink) {
-          if constexpr (PAIR) {
+          if constexpr (MODE == TS_HVP) {
+            if constexpr (PAIR)
+              elem_pair_hvp<std::decay_t<decltype(sink)>, PREP>(
+                  c, reinterpret_cast<const double*>(Gs), reinterpret_cast<const double*>(a.u),
+                  reinterpret_cast<const double*>(a.v), fb2, sink, bad);
+            else
+              elem_native_hvp<T>(c, Gs, a.u, a.v, fb, sink);
+          } else if constexpr (PAIR) {
             elem_pair<MODE, std::decay_t<decltype(sink)>, PREP>(c, reinterpret_cast<const double*>(Gs),
                             reinterpret_cast<const double*>(a.u), fb2, tab, a.K, facc_p, sink,
                             reinterpret_cast<double*>(a.tape) + e * 4, bad);
@@ -365,7 +374,7 @@ static cudaError_t launch_ts_k(const kg_problem* p, const TsArgs<T>& a, cudaStre
 
 template <typename T, bool PAIR, int MODE, bool PREP>
 static cudaError_t launch_ts_p(const kg_problem* p, const TsArgs<T>& a, cudaStream_t s) {
-  if constexpr (MODE == TS_GRAD) {
+  if constexpr (MODE == TS_GRAD || MODE == TS_HVP) {
     if (p->strategy == KG_STRATEGY_SHARED) return launch_ts_k<T, PAIR, MODE, SC_SHARED, PREP>(p, a, s);
     if (p->strategy == KG_STRATEGY_WARP) return launch_ts_k<T, PAIR, MODE, SC_WARP, PREP>(p, a, s);
   }
@@ -387,21 +396,24 @@ static cudaError_t dispatch_ts(const kg_problem* p, int mode, const TsArgs<T>& a
     if constexpr (sizeof(T) == 8) {
       if (mode == TS_EVAL) return launch_ts<T, true, TS_EVAL>(p, a, s);
       if (mode == TS_GRAD) return launch_ts<T, true, TS_GRAD>(p, a, s);
+      if (mode == TS_HVP) return launch_ts<T, true, TS_HVP>(p, a, s);
       return launch_ts<T, true, TS_TAPE>(p, a, s);
     }
   }
   if (mode == TS_EVAL) return launch_ts<T, false, TS_EVAL>(p, a, s);
   if (mode == TS_GRAD) return launch_ts<T, false, TS_GRAD>(p, a, s);
+  if (mode == TS_HVP) return launch_ts<T, false, TS_HVP>(p, a, s);
   return launch_ts<T, false, TS_TAPE>(p, a, s);
 }
 
 template <typename T>
 static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, void* gx,
-                              const void* seed, cudaStream_t s) {
+                              const void* seed, const void* v, cudaStream_t s) {
   TsArgs<T> a{};
   a.conn = static_cast<const int4*>(p->data0);
   a.G = static_cast<const T*>(p->aprep ? p->aprep : p->data1);
   a.u = static_cast<const T*>(x);
+  a.v = static_cast<const T*>(v);
   a.ne = p->m;
   a.nv = (int)p->n;
   a.seed = static_cast<const T*>(seed);
@@ -417,8 +429,8 @@ static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, v
     kg_status rc = logtab_for_device(&a.logtab);
     if (rc != KG_OK) return rc;
   }
-  static const char* names[3] = {"tet_staged_kernel<eval>", "tet_staged_kernel<grad>",
-                                 "tet_staged_kernel<tape>"};
+  static const char* names[4] = {"tet_staged_kernel<eval>", "tet_staged_kernel<grad>",
+                                 "tet_staged_kernel<tape>", "tet_staged_kernel<hvp>"};
   prof_begin(s, names[mode]);
   cudaError_t e = dispatch_ts<T>(p, mode, a, s);
   prof_end(s);
@@ -427,9 +439,9 @@ static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, v
 }
 
 kg_status tet_staged(kg_problem* p, int mode, const void* x, void* f, void* gx, const void* seed,
-                     cudaStream_t s) {
-  return p->dtype == KG_F64 ? tet_staged_t<double>(p, mode, x, f, gx, seed, s)
-                            : tet_staged_t<float>(p, mode, x, f, gx, seed, s);
+                     cudaStream_t s, const void* v) {
+  return p->dtype == KG_F64 ? tet_staged_t<double>(p, mode, x, f, gx, seed, v, s)
+                            : tet_staged_t<float>(p, mode, x, f, gx, seed, v, s);
 }
 
 }  // namespace kg
