@@ -57,6 +57,7 @@ struct BInst {
   int64_t m;  // dense: rows; tet: elements
   int ntiles;
   int team;   // dense: 32 or 256
+  int prep;   // pair batches: d0 (dense A) or d1 (tet G) is the prepared float-pair copy
   const void* d0;
   const void* d1;
   const void* x;
@@ -95,9 +96,14 @@ __device__ __forceinline__ void prefetch_range_l2(const void* p, size_t bytes) {
   }
 }
 
-template <bool PAIR, typename T>
+// PREP: v holds the 8 bytes of a prepared float pair (h in the low word, l in
+// the high word), read as a double: two register moves instead of a split.
+template <bool PAIR, typename T, bool PREP = false>
 __device__ __forceinline__ void b_split(T v, float& h, float& l) {
-  if constexpr (PAIR) {
+  if constexpr (PAIR && PREP) {
+    h = __int_as_float(__double2loint((double)v));
+    l = __int_as_float(__double2hiint((double)v));
+  } else if constexpr (PAIR) {
     const Pair p = split_f64((double)v);
     h = p.h;
     l = p.l;
@@ -116,7 +122,7 @@ __device__ __forceinline__ void team_barrier(int team) {
 }
 
 // Rows [w.start, w.start + w.count) of a dense instance; returns the tile's f.
-template <typename T, bool PAIR, int TEAM>
+template <typename T, bool PAIR, int TEAM, bool PREP>
 __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp, double* red,
                              bool& bad) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -169,7 +175,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
 #pragma unroll
     for (int k = 0; k < B_CPT; ++k) {
       if constexpr (PAIR) {
-        if (k < cpt) b_split<PAIR>(av[k], ah[k], al[k]);
+        if (k < cpt) b_split<PAIR, T, PREP>(av[k], ah[k], al[k]);
         else ah[k] = al[k] = 0.f;
       }
     }
@@ -290,7 +296,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
 }
 
 // Elements [w.start, w.start + w.count) of a tet instance; returns the tile's f.
-template <typename T, bool PAIR, bool WARPC>
+template <typename T, bool PAIR, bool WARPC, bool PREP>
 __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, const LogConsts& K,
                            double* red, bool& bad) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -306,9 +312,10 @@ __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, co
     for (int64_t e = w.start + tid; e < e1; e += BT, ++cnt) {
       const int4 c = __ldcs(conn + e);
       if constexpr (PAIR) {
-        elem_pair<TS_GRAD>(c, reinterpret_cast<const double*>(G) + e * 12,
-                           reinterpret_cast<const double*>(u), Pair{2.0f, 0.0f}, tab, K, fp,
-                           AtomicSink<double>{reinterpret_cast<double*>(gu)}, nullptr, bad);
+        elem_pair<TS_GRAD, AtomicSink<double>, PREP>(
+            c, reinterpret_cast<const double*>(G) + e * 12, reinterpret_cast<const double*>(u),
+            Pair{2.0f, 0.0f}, tab, K, fp, AtomicSink<double>{reinterpret_cast<double*>(gu)}, nullptr,
+            bad);
         if ((cnt & 31) == 31) acc_renorm(fp);
       } else {
         elem_native<T, TS_GRAD>(c, G + e * 12, u, T(1), fn, AtomicSink<T>{gu}, nullptr);
@@ -325,9 +332,9 @@ __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, co
     if (act) {
       c = __ldcs(conn + e);
       if constexpr (PAIR) {
-        elem_pair<TS_GRAD>(c, reinterpret_cast<const double*>(G) + e * 12,
-                           reinterpret_cast<const double*>(u), Pair{2.0f, 0.0f}, tab, K, fp,
-                           CollectSink<T>{cv, cpr}, nullptr, bad);
+        elem_pair<TS_GRAD, CollectSink<T>, PREP>(
+            c, reinterpret_cast<const double*>(G) + e * 12, reinterpret_cast<const double*>(u),
+            Pair{2.0f, 0.0f}, tab, K, fp, CollectSink<T>{cv, cpr}, nullptr, bad);
         if ((cnt & 31) == 31) acc_renorm(fp);
       } else {
         elem_native<T, TS_GRAD>(c, G + e * 12, u, T(1), fn, CollectSink<T>{cv, cpr}, nullptr);
@@ -363,6 +370,24 @@ __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, co
     const double t = block_sum((double)fn, red);
     __syncthreads();
     return t;
+  }
+}
+
+template <typename T, bool PAIR, bool PREP>
+__device__ __forceinline__ double dense_dispatch(const BInst& I, const BItem& w, unsigned char* wsp,
+                                                 double* red, bool& bad) {
+  if constexpr (PREP && !PAIR) {
+    return 0.0;  // not instantiated: prepared copies exist for pair batches only
+  } else {
+    switch (I.team) {
+      case 4: return dense_tile<T, PAIR, 4, PREP>(I, w, wsp, red, bad);
+      case 8: return dense_tile<T, PAIR, 8, PREP>(I, w, wsp, red, bad);
+      case 16: return dense_tile<T, PAIR, 16, PREP>(I, w, wsp, red, bad);
+      case 32: return dense_tile<T, PAIR, 32, PREP>(I, w, wsp, red, bad);
+      case 64: return dense_tile<T, PAIR, 64, PREP>(I, w, wsp, red, bad);
+      case 128: return dense_tile<T, PAIR, 128, PREP>(I, w, wsp, red, bad);
+      default: return dense_tile<T, PAIR, BT, PREP>(I, w, wsp, red, bad);
+    }
   }
 }
 
@@ -428,18 +453,13 @@ __global__ void __launch_bounds__(BT) batched_kernel(BArgs a) {
       }
     }
     double ft;
+    const bool prep = PAIR && I.prep;
     if (I.kind == BK_DENSE) {
-      switch (I.team) {
-        case 4: ft = dense_tile<T, PAIR, 4>(I, w, wsp, red, bad); break;
-        case 8: ft = dense_tile<T, PAIR, 8>(I, w, wsp, red, bad); break;
-        case 16: ft = dense_tile<T, PAIR, 16>(I, w, wsp, red, bad); break;
-        case 32: ft = dense_tile<T, PAIR, 32>(I, w, wsp, red, bad); break;
-        case 64: ft = dense_tile<T, PAIR, 64>(I, w, wsp, red, bad); break;
-        case 128: ft = dense_tile<T, PAIR, 128>(I, w, wsp, red, bad); break;
-        default: ft = dense_tile<T, PAIR, BT>(I, w, wsp, red, bad); break;
-      }
+      ft = prep ? dense_dispatch<T, PAIR, true>(I, w, wsp, red, bad)
+                : dense_dispatch<T, PAIR, false>(I, w, wsp, red, bad);
     } else {
-      ft = tet_tile<T, PAIR, WARPC>(I, w, tab, a.K, red, bad);
+      ft = prep ? tet_tile<T, PAIR, WARPC, true>(I, w, tab, a.K, red, bad)
+                : tet_tile<T, PAIR, WARPC, false>(I, w, tab, a.K, red, bad);
     }
     if (tid == 0) I.fpart[w.tile] = ft;
     __threadfence();
@@ -568,6 +588,11 @@ Plan make_plan(const std::vector<kg_problem*>& probs, const std::vector<int>& id
     I.m = p->m;
     I.d0 = p->data0;
     I.d1 = p->data1;
+    if (pair && p->aprep && p->arith == KG_ARITH_PAIR) {  // stream the prepared float pairs
+      I.prep = 1;
+      if (p->kind == KG_QUADFORM) I.d0 = p->aprep;
+      else I.d1 = p->aprep;
+    }
     int64_t per;
     if (I.kind == BK_DENSE) {
       auto f = tu.dense_rows.find(bucket_of(p->n));
