@@ -148,11 +148,13 @@ typedef struct {
   int tile;                 /* elements (tet) or rows (dense) per work tile; 0 = tuned */
   size_t tape_budget_bytes; /* cap on optional create-time workspaces; 0 = 1 GiB.
                              * FP64 problems in PAIR arithmetic first take a copy
-                             * of A (QUADFORM, 8 m n bytes) or G (TETENERGY,
-                             * 96 N_e bytes) split into float pairs, which the
-                             * kernels stream instead of splitting on every
-                             * call; KG_MODE_AUTO then takes the tet tape if it
-                             * fits what is left */
+                             * of A (QUADFORM, 8 m n bytes), G (TETENERGY,
+                             * 96 N_e bytes) or the stored values (SPQUADFORM,
+                             * 8 nnz bytes; required by its pair kernels, so
+                             * AUTO stays NATIVE without it) split into float
+                             * pairs, which the kernels stream instead of
+                             * splitting on every call; KG_MODE_AUTO then takes
+                             * the tet tape if it fits what is left */
 } kg_options;
 
 typedef struct kg_problem kg_problem;

@@ -33,11 +33,12 @@ SHAPES = [(1, 1, (1, 1)), (7, 5, (0, 4)), (300, 200, (0, 9)), (5000, 3000, (8, 2
 
 @pytest.mark.parametrize("m,n,deg", SHAPES)
 @pytest.mark.parametrize("strategy", ["atomic", "transpose"])
-def test_f64_matches_oracle(api, m, n, deg, strategy):
+@pytest.mark.parametrize("arith", ["pair", "native"])
+def test_f64_matches_oracle(api, m, n, deg, strategy, arith):
     A, x = W.spquadform_inputs(m, n, d_lo=deg[0], d_hi=deg[1], seed=m + n)
     f_ref, g_ref, gv_ref = O.spquadform_grad(A.rowptr, A.col, A.val, x, fbar=0.5, want_gval=True)
-    p = _problem(api, A, strategy=strategy)
-    assert p.config[0] == strategy
+    p = _problem(api, A, strategy=strategy, arith=arith)
+    assert p.config[0] == strategy and p.config[2] == arith
     xt = torch.tensor(x, device="cuda")
     gval = torch.empty(A.nnz, dtype=torch.float64, device="cuda")
     f, g = p.grad(xt, gdata=gval, seed=torch.tensor(0.5, dtype=torch.float64, device="cuda"))
@@ -130,12 +131,40 @@ def test_edge_cases(api):
     q = api.SpQuadForm(torch.tensor([0, 1], dtype=torch.int32, device=dev),
                        torch.tensor([0], dtype=torch.int32, device=dev),
                        torch.ones(1, dtype=torch.float64, device=dev), 2)
-    assert q.config == ("atomic", "recompute", "native")
+    assert q.config == ("atomic", "recompute", "pair")
     with pytest.raises(L.KGError) as ei:
         api.SpQuadForm(torch.tensor([0, 1], dtype=torch.int32, device=dev),
                        torch.tensor([0], dtype=torch.int32, device=dev),
                        torch.ones(1, dtype=torch.float64, device=dev), 2, strategy="csr")
     assert ei.value.status == L.KG_ERR_UNSUPPORTED
+
+
+def test_pair_range_rules(api):
+    from paper_2507_13204_gb300 import _lib as L
+    A, x = W.spquadform_inputs(2000, 1500, seed=21)
+    A.val[17] = 1e-70  # below the pair range: AUTO falls back to native FP64
+    p = _problem(api, A)
+    assert p.config[2] == "native"
+    f, g = p.grad(torch.tensor(x, device="cuda"))
+    p.sync()
+    assert rel_l2(g.cpu().numpy(), O.spquadform_grad(A.rowptr, A.col, A.val, x)[1]) <= TOL["f64"]
+    with pytest.raises(L.KGError) as ei:
+        _problem(api, A, arith="pair")
+    assert ei.value.status == L.KG_ERR_UNSUPPORTED
+    # an x out of range is reported through kg_sync; the next good call is clean
+    A.val[17] = 0.5
+    q = _problem(api, A, arith="pair")
+    xb = x.copy()
+    xb[A.col[5]] = 1e300
+    q.grad(torch.tensor(xb, device="cuda"))
+    with pytest.raises(L.KGError) as ei:
+        q.sync()
+    assert ei.value.status == L.KG_ERR_RANGE
+    q.grad(torch.tensor(x, device="cuda"))
+    q.sync()
+    # the prepared copy is 8 bytes per stored value; with a smaller budget AUTO stays native
+    small = _problem(api, A, tape_budget_bytes=8 * A.nnz - 8)
+    assert small.config[2] == "native"
 
 
 @pytest.mark.parametrize("team", [2, 4, 16, 32])
