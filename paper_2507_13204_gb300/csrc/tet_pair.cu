@@ -331,11 +331,6 @@ int tet_staged_grid(const kg_problem* p) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)num_sms() * TS_MAX_PER_SM));
 }
 
-static int ts_cap() {
-  static const int v = [] { const char* e = getenv("KG_TET_CAP"); return e ? atoi(e) : 0; }();
-  return v;
-}
-
 // `occ` caches the kernel's resident CTAs per SM (queried on first use).
 template <typename K>
 static int ts_grid_for(const kg_problem* p, K kern, size_t smem, int& occ_cache) {
@@ -345,8 +340,7 @@ static int ts_grid_for(const kg_problem* p, K kern, size_t smem, int& occ_cache)
       o = 1;
     occ_cache = std::max(o, 1);
   }
-  int occ = occ_cache;
-  if (ts_cap() > 0) occ = std::min(occ, ts_cap());
+  const int occ = occ_cache;
   const int64_t ntiles = (p->m + TS_THREADS - 1) / TS_THREADS;
   const int64_t g = std::min<int64_t>(ntiles, (int64_t)num_sms() * std::min(occ, TS_MAX_PER_SM));
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, p->tet_grid));
