@@ -13,6 +13,8 @@
 
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "kg_device.cuh"
 #include "kg_pair.cuh"
 
@@ -34,6 +36,15 @@ __device__ __forceinline__ float shfl_v(float v, int src) { return __shfl_sync(0
 __device__ __forceinline__ double shfl_v(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
 __device__ __forceinline__ Acc shfl_v(Acc v, int src) {
   return Acc{__shfl_sync(0xffffffffu, v.s, src), __shfl_sync(0xffffffffu, v.l, src)};
+}
+__device__ __forceinline__ float shfl_down_v(float v, int d) {
+  return __shfl_down_sync(0xffffffffu, v, d);
+}
+__device__ __forceinline__ double shfl_down_v(double v, int d) {
+  return __shfl_down_sync(0xffffffffu, v, d);
+}
+__device__ __forceinline__ Acc shfl_down_v(Acc v, int d) {
+  return Acc{__shfl_down_sync(0xffffffffu, v.s, d), __shfl_down_sync(0xffffffffu, v.l, d)};
 }
 
 template <typename T>
@@ -62,25 +73,43 @@ __device__ __forceinline__ void sink_pair(const CollectSink<T>& gu, int k, int, 
 }
 
 // Warp-level combine of one contribution per lane: lanes whose key (vertex)
-// is equal form a group (match.any); every lane walks the group members above
-// it, adding their values (shuffles), so the lowest lane of each group ends
-// with the group total and adds it to gu with one atomic.  Inactive lanes take
-// part in the shuffles only.  All 32 lanes must call it together.
+// is equal form a group (match.any), and the lowest lane of each group adds
+// the group total to gu with one atomic.  Inactive lanes take part in the
+// shuffles only.  All 32 lanes must call it together.
+//   - float-pair or FP64 values (an add costs ~10 instructions or the FP64
+//     unit), every group a contiguous
+//     run of lanes (elements numbered along the mesh): a segmented suffix
+//     scan, ceil(log2 of the longest run) steps of shift-down adds that stay
+//     inside the run;
+//   - otherwise: every lane walks the group members above it, one shuffle
+//     round per member (for plain floats this is cheaper than the extra votes
+//     the scan needs).
 template <typename V, typename AddF, typename FlushF>
 __device__ __forceinline__ void warp_combine(bool active, int key, V val, AddF add, FlushF flush) {
   const int lane = threadIdx.x & 31;
   const unsigned peers = __match_any_sync(0xffffffffu, active ? key : -1);
-  unsigned rest = active ? peers & (0xFFFFFFFEu << lane) : 0u;
+  const int first = __ffs(peers) - 1, last = 31 - __clz(peers);
+  const unsigned run = (last == 31 ? 0xFFFFFFFFu : ((2u << last) - 1u)) & ~((1u << first) - 1u);
   V acc = val;
-  while (__any_sync(0xffffffffu, rest != 0u)) {
-    const int src = rest ? __ffs(rest) - 1 : lane;
-    const V other = shfl_v(val, src);
-    if (rest) {
-      acc = add(acc, other);
-      rest &= rest - 1u;
+  constexpr bool kScan = !std::is_same<V, float>::value;  // pairs and FP64 adds
+  if (kScan && __all_sync(0xffffffffu, peers == run)) {
+    const int span = (int)__reduce_max_sync(0xffffffffu, (unsigned)(last - first + 1));
+    for (int d = 1; d < span; d <<= 1) {
+      const V other = shfl_down_v(acc, d);
+      if (lane + d <= last) acc = add(acc, other);
+    }
+  } else {
+    unsigned rest = active ? peers & (0xFFFFFFFEu << lane) : 0u;
+    while (__any_sync(0xffffffffu, rest != 0u)) {
+      const int src = rest ? __ffs(rest) - 1 : lane;
+      const V other = shfl_v(val, src);
+      if (rest) {
+        acc = add(acc, other);
+        rest &= rest - 1u;
+      }
     }
   }
-  if (active && (peers & ((1u << lane) - 1u)) == 0u) flush(key, acc);
+  if (active && lane == first) flush(key, acc);
 }
 
 // Per-tile table of (vertex, partial sum) in shared memory.  keys[] holds -1
