@@ -76,6 +76,7 @@ struct kg_problem {
   int* rowptr = nullptr;     // tet CSR: [N_v + 1]; sparse CSC: colptr [n + 1]
   int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k; sparse CSC: row of each entry
   void* valT = nullptr;      // sparse CSC: values in column order
+  void* usplit = nullptr;    // tet pair: u and v as float pairs [2][N_v], split per call
   void* xdev = nullptr;      // kg_grad_host staging
   void* gdev = nullptr;
   void* fdev = nullptr;
@@ -124,8 +125,9 @@ LogConsts log_consts();
 // product in direction v
 int tet_staged_grid(const kg_problem* p);
 kg_status tet_staged_setup(kg_problem* p);
+// zero_gx: gx is zeroed by the pair kernels' vertex-split launch (pair GRAD / HVP only)
 kg_status tet_staged(kg_problem* p, int mode, const void* x, void* f, void* gx, const void* seed,
-                     cudaStream_t s, const void* v = nullptr);
+                     cudaStream_t s, const void* v = nullptr, bool zero_gx = false);
 
 kg_status tet_setup(kg_problem* p, cudaStream_t s);
 kg_status tet_eval(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s);

@@ -208,7 +208,9 @@ __device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ 
 
 // One element in float-pair arithmetic (FP64 data).  Gs points at the
 // element's 12 doubles, or (PREP) at its 12 float pairs (h, l) prepared once.
-template <int MODE, typename Sink, bool PREP = false>
+// USPLIT: u points at float pairs of the vertex values, split (and range
+// checked) once per call by pair_split_vec instead of once per gather.
+template <int MODE, typename Sink, bool PREP = false, bool USPLIT = false>
 __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict__ Gs,
                                           const double* __restrict__ u, Pair fb2,
                                           const float4* __restrict__ tab, const LogConsts& K,
@@ -226,12 +228,21 @@ __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict
       G[i + 1] = split_f64(v.y);
     }
   }
-  const double ud[4] = {__ldg(u + c.x), __ldg(u + c.y), __ldg(u + c.z), __ldg(u + c.w)};
   Pair U[4];
+  if constexpr (USPLIT) {
+    const float2* up = reinterpret_cast<const float2*>(u);
+    const float2 q0 = __ldg(up + c.x), q1 = __ldg(up + c.y), q2 = __ldg(up + c.z), q3 = __ldg(up + c.w);
+    U[0] = Pair{q0.x, q0.y};
+    U[1] = Pair{q1.x, q1.y};
+    U[2] = Pair{q2.x, q2.y};
+    U[3] = Pair{q3.x, q3.y};
+  } else {
+    const double ud[4] = {__ldg(u + c.x), __ldg(u + c.y), __ldg(u + c.z), __ldg(u + c.w)};
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    bad |= !pair_in_range(ud[k]);
-    U[k] = split_f64(ud[k]);
+    for (int k = 0; k < 4; ++k) {
+      bad |= !pair_in_range(ud[k]);
+      U[k] = split_f64(ud[k]);
+    }
   }
   Pair g[3];
 #pragma unroll
@@ -310,7 +321,7 @@ __device__ __forceinline__ void elem_native_hvp(const int4 c, const T* __restric
 }
 
 // The same in float-pair arithmetic (FP64 data); fb2 = 2 fbar as a pair.
-template <typename Sink, bool PREP = false>
+template <typename Sink, bool PREP = false, bool USPLIT = false>
 __device__ __forceinline__ void elem_pair_hvp(const int4 c, const double* __restrict__ Gs,
                                               const double* __restrict__ u,
                                               const double* __restrict__ v, Pair fb2,
@@ -332,10 +343,17 @@ __device__ __forceinline__ void elem_pair_hvp(const int4 c, const double* __rest
   Pair U[4], V[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    const double uk = __ldg(u + idx[k]), vk = __ldg(v + idx[k]);
-    bad |= !pair_in_range(uk) || !pair_in_range(vk);
-    U[k] = split_f64(uk);
-    V[k] = split_f64(vk);
+    if constexpr (USPLIT) {
+      const float2 qu = __ldg(reinterpret_cast<const float2*>(u) + idx[k]);
+      const float2 qv = __ldg(reinterpret_cast<const float2*>(v) + idx[k]);
+      U[k] = Pair{qu.x, qu.y};
+      V[k] = Pair{qv.x, qv.y};
+    } else {
+      const double uk = __ldg(u + idx[k]), vk = __ldg(v + idx[k]);
+      bad |= !pair_in_range(uk) || !pair_in_range(vk);
+      U[k] = split_f64(uk);
+      V[k] = split_f64(vk);
+    }
   }
   Pair g[3], gd[3];
 #pragma unroll

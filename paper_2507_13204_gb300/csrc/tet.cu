@@ -300,13 +300,15 @@ static kg_status tet_grad_t(kg_problem* p, const void* x, void* f, void* gx, con
     if (rc != KG_OK) return rc;
     return tet_scatter_t<T>(p, gx, seed, accumulate, s);
   }
+  // pair arithmetic: the kernel that splits u also zeroes gu (one launch for both)
+  const bool fold_zero = p->arith == KG_ARITH_PAIR && sizeof(T) == 8;
   cudaError_t e;
-  if (!accumulate) {
+  if (!accumulate && !fold_zero) {
     if ((e = cudaMemsetAsync(gx, 0, sizeof(T) * (size_t)p->n, s)) != cudaSuccess)
       return cuda_fail(e, "zero gu");
     count_launch();
   }
-  return tet_staged(p, 1, x, f, gx, seed, s);
+  return tet_staged(p, 1, x, f, gx, seed, s, nullptr, fold_zero && !accumulate);
 }
 
 kg_status tet_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
@@ -317,12 +319,13 @@ kg_status tet_grad(kg_problem* p, const void* x, void* f, void* gx, const void* 
 
 kg_status tet_hvp(kg_problem* p, const void* x, const void* v, void* hv, const void* seed,
                   int accumulate, cudaStream_t s) {
-  if (!accumulate) {
+  const bool fold_zero = p->arith == KG_ARITH_PAIR && p->dtype == KG_F64;
+  if (!accumulate && !fold_zero) {
     cudaError_t e = cudaMemsetAsync(hv, 0, p->esize * (size_t)p->n, s);
     if (e != cudaSuccess) return cuda_fail(e, "zero hv");
     count_launch();
   }
-  return tet_staged(p, 3, x, nullptr, hv, seed, s, v);
+  return tet_staged(p, 3, x, nullptr, hv, seed, s, v, fold_zero && !accumulate);
 }
 
 kg_status tet_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate,

@@ -180,13 +180,14 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
         auto run = [&](const auto& sink) {
           if constexpr (MODE == TS_HVP) {
             if constexpr (PAIR)
-              elem_pair_hvp<std::decay_t<decltype(sink)>, PREP>(
+              elem_pair_hvp<std::decay_t<decltype(sink)>, PREP, true>(
                   c, reinterpret_cast<const double*>(Gs), reinterpret_cast<const double*>(a.u),
                   reinterpret_cast<const double*>(a.v), fb2, sink, bad);
             else
               elem_native_hvp<T>(c, Gs, a.u, a.v, fb, sink);
           } else if constexpr (PAIR) {
-            elem_pair<MODE, std::decay_t<decltype(sink)>, PREP>(c, reinterpret_cast<const double*>(Gs),
+            elem_pair<MODE, std::decay_t<decltype(sink)>, PREP, MODE == TS_GRAD>(
+                            c, reinterpret_cast<const double*>(Gs),
                             reinterpret_cast<const double*>(a.u), fb2, tab, a.K, facc_p, sink,
                             reinterpret_cast<double*>(a.tape) + e * 4, bad);
             if ((i & 31) == 31) acc_renorm(facc_p);
@@ -266,6 +267,31 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
     fcta = block_sum((double)facc_n, red);
   }
   finish_sum<T>(fcta, a.fpart, a.counter, a.f, 0, red);
+}
+
+// Float pairs of the vertex vector u (and v), once per call for the pair
+// gradient and Hessian-vector kernels (which then gather 8-byte pairs instead
+// of splitting ~24 gathered doubles per vertex), with the zeroing of the output
+// folded in; values outside the pair range set ERRBIT_RANGE.
+__global__ void pair_split_vec_kernel(const double* __restrict__ u, const double* __restrict__ v,
+                                      int64_t n, float2* us, float2* vs, double* zero,
+                                      unsigned* err) {
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double d = __ldg(u + i);
+    bad |= !pair_in_range(d);
+    const Pair p = split_f64(d);
+    us[i] = make_float2(p.h, p.l);
+    if (v) {
+      const double dv = __ldg(v + i);
+      bad |= !pair_in_range(dv);
+      const Pair q = split_f64(dv);
+      vs[i] = make_float2(q.h, q.l);
+    }
+    if (zero) zero[i] = 0.0;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_error(err, ERRBIT_RANGE);
 }
 
 // ---------------------------------------------------------------- host ----
@@ -351,6 +377,9 @@ kg_status tet_staged_setup(kg_problem* p) {
     const float4* t = nullptr;
     kg_status rc = logtab_for_device(&t);
     if (rc != KG_OK) return rc;
+    // u and v as float pairs (16 N_v bytes), split per call
+    if ((rc = ws_alloc(p, &p->usplit, 16 * (size_t)p->n, "vertex values as float pairs")) != KG_OK)
+      return rc;
   }
   return KG_OK;
 }
@@ -402,7 +431,7 @@ static cudaError_t dispatch_ts(const kg_problem* p, int mode, const TsArgs<T>& a
 
 template <typename T>
 static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, void* gx,
-                              const void* seed, const void* v, cudaStream_t s) {
+                              const void* seed, const void* v, bool zero_gx, cudaStream_t s) {
   TsArgs<T> a{};
   a.conn = static_cast<const int4*>(p->data0);
   a.G = static_cast<const T*>(p->aprep ? p->aprep : p->data1);
@@ -422,6 +451,19 @@ static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, v
   if (sizeof(T) == 8 && p->arith == KG_ARITH_PAIR) {
     kg_status rc = logtab_for_device(&a.logtab);
     if (rc != KG_OK) return rc;
+    if (mode == TS_GRAD || mode == TS_HVP) {  // u (and v) read as float pairs split here
+      float2* us = static_cast<float2*>(p->usplit);
+      const int g =
+          (int)std::max<int64_t>(1, std::min<int64_t>((p->n + 255) / 256, (int64_t)num_sms() * 8));
+      pair_split_vec_kernel<<<g, 256, 0, s>>>(static_cast<const double*>(x),
+                                              static_cast<const double*>(v), p->n, us, us + p->n,
+                                              zero_gx ? static_cast<double*>(gx) : nullptr, p->err);
+      count_launch();
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "split vertex values");
+      a.u = reinterpret_cast<const T*>(us);
+      a.v = v ? reinterpret_cast<const T*>(us + p->n) : nullptr;
+    }
   }
   static const char* names[4] = {"tet_staged_kernel<eval>", "tet_staged_kernel<grad>",
                                  "tet_staged_kernel<tape>", "tet_staged_kernel<hvp>"};
@@ -433,9 +475,9 @@ static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, v
 }
 
 kg_status tet_staged(kg_problem* p, int mode, const void* x, void* f, void* gx, const void* seed,
-                     cudaStream_t s, const void* v) {
-  return p->dtype == KG_F64 ? tet_staged_t<double>(p, mode, x, f, gx, seed, v, s)
-                            : tet_staged_t<float>(p, mode, x, f, gx, seed, v, s);
+                     cudaStream_t s, const void* v, bool zero_gx) {
+  return p->dtype == KG_F64 ? tet_staged_t<double>(p, mode, x, f, gx, seed, v, zero_gx, s)
+                            : tet_staged_t<float>(p, mode, x, f, gx, seed, v, zero_gx, s);
 }
 
 }  // namespace kg
