@@ -100,7 +100,9 @@ __device__ __forceinline__ void warp_combine(bool active, int key, V val, AddF a
     }
   } else {
     unsigned rest = active ? peers & (0xFFFFFFFEu << lane) : 0u;
-    while (__any_sync(0xffffffffu, rest != 0u)) {
+    // rounds = the largest group's size - 1, from one reduction instead of a vote per round
+    const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(rest));
+    for (int r = 0; r < rounds; ++r) {
       const int src = rest ? __ffs(rest) - 1 : lane;
       const V other = shfl_v(val, src);
       if (rest) {

@@ -18,6 +18,7 @@
 
 #include "kg_device.cuh"
 #include "kg_internal.h"
+#include "kg_pair.cuh"
 #include "kg_tet_elem.cuh"
 
 namespace kg {
@@ -59,6 +60,121 @@ __global__ void __launch_bounds__(256) tet_tape_scatter_kernel(const int4* __res
       }
     }
   }
+}
+
+// FP32 kernels without shared-memory staging (the staged kernel's tiles are
+// limited by shared memory to 4 CTAs per SM; these run 6).  Each thread takes
+// two elements per step: their conn (int4) and G (three float4) are streamed
+// with no L1 allocation and all of their loads and u (and v) gathers are
+// issued before any is used.  Lanes of a warp hold consecutive elements, so
+// the warp combine of the scatter sees the mesh order.  Modes as the staged
+// kernel: forward, gradient (warp-combined or plain atomics), tape, Hessian-
+// vector product.
+struct DirectArgs {
+  const int4* conn;
+  const float4* G;
+  const float* u;
+  const float* v;
+  int64_t ne;
+  const float* seed;
+  float* gu;
+  float* tape;
+  double* fpart;
+  unsigned* counter;
+  float* f;
+};
+
+template <int MODE, bool WARPC>
+__global__ void __launch_bounds__(256) tet_direct_f32_kernel(DirectArgs a) {
+  __shared__ double red[32];
+  constexpr bool REV = MODE == TS_GRAD || MODE == TS_HVP;
+  const int lane = threadIdx.x & 31;
+  const float fb = REV ? load_seed(a.seed) : 1.f;
+  float fa = 0.f, fc = 0.f;  // TwoSum-compensated float sum of f_e
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // warp-uniform trip count: the loop runs on the warp's first element
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.ne;
+       base += 2 * stride) {
+    int4 c[2];
+    float4 g[2][3];
+    bool act[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int64_t e = base + lane + h * stride;
+      act[h] = e < a.ne;
+      c[h] = act[h] ? __ldcs(a.conn + e) : make_int4(0, 0, 0, 0);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) g[h][q] = act[h] ? __ldcs(a.G + e * 3 + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    float uv[2][4], vv[2][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uv[h][0] = __ldg(a.u + c[h].x);  // vertex 0 for inactive lanes (N_v >= 1)
+      uv[h][1] = __ldg(a.u + c[h].y);
+      uv[h][2] = __ldg(a.u + c[h].z);
+      uv[h][3] = __ldg(a.u + c[h].w);
+      if constexpr (MODE == TS_HVP) {
+        vv[h][0] = __ldg(a.v + c[h].x);
+        vv[h][1] = __ldg(a.v + c[h].y);
+        vv[h][2] = __ldg(a.v + c[h].z);
+        vv[h][3] = __ldg(a.v + c[h].w);
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float gg[3], gd[3];
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        gg[q] = g[h][q].x * uv[h][0] + g[h][q].y * uv[h][1] + g[h][q].z * uv[h][2] + g[h][q].w * uv[h][3];
+        if constexpr (MODE == TS_HVP)
+          gd[q] = g[h][q].x * vv[h][0] + g[h][q].y * vv[h][1] + g[h][q].z * vv[h][2] + g[h][q].w * vv[h][3];
+      }
+      const float sq = gg[0] * gg[0] + gg[1] * gg[1] + gg[2] * gg[2];
+      float hq[3];  // the vector that G^T maps to the element's four contributions
+      if constexpr (MODE != TS_HVP) {
+        if (act[h]) {
+          float t, r;
+          two_sum(fa, log1pf(sq), t, r);
+          fa = t;
+          fc += r;
+        }
+        const float w = 2.f * fb / (1.f + sq);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) hq[q] = w * gg[q];
+      } else {
+        const float t1 = 1.f + sq;
+        const float w = 2.f * fb / t1;
+        const float sd = 2.f * (gg[0] * gd[0] + gg[1] * gd[1] + gg[2] * gd[2]);
+        const float wd = -w * sd / t1;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) hq[q] = wd * gg[q] + w * gd[q];
+      }
+      if constexpr (MODE != TS_EVAL) {
+        float cv[4];
+        cv[0] = g[h][0].x * hq[0] + g[h][1].x * hq[1] + g[h][2].x * hq[2];
+        cv[1] = g[h][0].y * hq[0] + g[h][1].y * hq[1] + g[h][2].y * hq[2];
+        cv[2] = g[h][0].z * hq[0] + g[h][1].z * hq[1] + g[h][2].z * hq[2];
+        cv[3] = g[h][0].w * hq[0] + g[h][1].w * hq[1] + g[h][2].w * hq[2];
+        const int key[4] = {c[h].x, c[h].y, c[h].z, c[h].w};
+        if constexpr (MODE == TS_TAPE) {
+          if (act[h])
+            reinterpret_cast<float4*>(a.tape)[base + lane + h * stride] =
+                make_float4(cv[0], cv[1], cv[2], cv[3]);
+        } else {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            if constexpr (WARPC) {
+              warp_combine(act[h], key[k], cv[k], [](float x, float y) { return x + y; },
+                           [&](int vtx, float tot) { atomicAdd(a.gu + vtx, tot); });
+            } else if (act[h]) {
+              atomicAdd(a.gu + key[k], cv[k]);
+            }
+          }
+        }
+      }
+    }
+  }
+  finish_sum<float>(block_sum((double)fa + (double)fc, red), a.fpart, a.counter, a.f, 0, red);
 }
 
 // Atomic-free reverse: thread per vertex gathers its incidences, in ascending
@@ -254,8 +370,68 @@ kg_status build_buckets(const int* keys, int64_t count, int nbins, int* binptr, 
   return KG_OK;
 }
 
+// FP32 problems without bounds checks run the direct kernels, except the
+// shared-memory-table strategy, which needs the staged tiles.
+static bool use_direct(const kg_problem* p) {
+  return p->dtype == KG_F32 && !p->opt.check && p->strategy != KG_STRATEGY_SHARED;
+}
+
+// One wave: the resident CTAs of this instantiation on every SM (queried once),
+// within the f partials sized at kg_create.
+template <int MODE, bool WARPC>
+static void launch_direct(const kg_problem* p, const DirectArgs& a, cudaStream_t s) {
+  static int occ = 0;
+  if (occ < 1) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, tet_direct_f32_kernel<MODE, WARPC>, 256, 0) !=
+        cudaSuccess)
+      o = 1;
+    occ = std::max(o, 1);
+  }
+  const int64_t g = std::min<int64_t>({(p->m + 511) / 512, (int64_t)num_sms() * occ,
+                                       (int64_t)p->fpart_len});
+  tet_direct_f32_kernel<MODE, WARPC><<<(int)std::max<int64_t>(g, 1), 256, 0, s>>>(a);
+}
+
+static kg_status tet_direct(kg_problem* p, int mode, const void* x, const void* v, void* f,
+                            void* gx, const void* seed, cudaStream_t s) {
+  DirectArgs a{};
+  a.conn = static_cast<const int4*>(p->data0);
+  a.G = static_cast<const float4*>(p->data1);
+  a.u = static_cast<const float*>(x);
+  a.v = static_cast<const float*>(v);
+  a.ne = p->m;
+  a.seed = static_cast<const float*>(seed);
+  a.gu = static_cast<float*>(gx);
+  a.tape = static_cast<float*>(p->tape);
+  a.fpart = p->fpart;
+  a.counter = p->counter;
+  a.f = static_cast<float*>(f);
+  const bool warp = p->strategy == KG_STRATEGY_WARP;
+  static const char* names[4] = {"tet_direct_f32_kernel<eval>", "tet_direct_f32_kernel<grad>",
+                                 "tet_direct_f32_kernel<tape>", "tet_direct_f32_kernel<hvp>"};
+  prof_begin(s, names[mode]);
+  switch (mode) {
+    case TS_EVAL: launch_direct<TS_EVAL, false>(p, a, s); break;
+    case TS_TAPE: launch_direct<TS_TAPE, false>(p, a, s); break;
+    case TS_GRAD:
+      if (warp) launch_direct<TS_GRAD, true>(p, a, s);
+      else launch_direct<TS_GRAD, false>(p, a, s);
+      break;
+    default:
+      if (warp) launch_direct<TS_HVP, true>(p, a, s);
+      else launch_direct<TS_HVP, false>(p, a, s);
+      break;
+  }
+  prof_end(s);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KG_OK : cuda_fail(e, names[mode]);
+}
+
 kg_status tet_eval(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s) {
-  kg_status rc = tet_staged(p, tape ? 2 : 0, x, f, nullptr, nullptr, s);
+  kg_status rc = use_direct(p) ? tet_direct(p, tape ? TS_TAPE : TS_EVAL, x, nullptr, f, nullptr, nullptr, s)
+                               : tet_staged(p, tape ? 2 : 0, x, f, nullptr, nullptr, s);
   if (rc == KG_OK && tape) p->tape_valid = true;
   return rc;
 }
@@ -308,6 +484,7 @@ static kg_status tet_grad_t(kg_problem* p, const void* x, void* f, void* gx, con
       return cuda_fail(e, "zero gu");
     count_launch();
   }
+  if (use_direct(p)) return tet_direct(p, TS_GRAD, x, nullptr, f, gx, seed, s);
   return tet_staged(p, 1, x, f, gx, seed, s, nullptr, fold_zero && !accumulate);
 }
 
@@ -325,6 +502,7 @@ kg_status tet_hvp(kg_problem* p, const void* x, const void* v, void* hv, const v
     if (e != cudaSuccess) return cuda_fail(e, "zero hv");
     count_launch();
   }
+  if (use_direct(p)) return tet_direct(p, TS_HVP, x, v, nullptr, hv, seed, s);
   return tet_staged(p, 3, x, nullptr, hv, seed, s, v, fold_zero && !accumulate);
 }
 

@@ -54,10 +54,26 @@ def test_f32_matches_oracle_on_rounded_inputs(api, strategy):
     conn = torch.tensor(mesh.conn, device="cuda")
     p = api.TetEnergy(conn, torch.tensor(G32, dtype=torch.float32, device="cuda"), mesh.nv,
                       strategy=strategy)
-    f, g = p.grad(torch.tensor(u32, dtype=torch.float32, device="cuda"))
+    ut = torch.tensor(u32, dtype=torch.float32, device="cuda")
+    f, g = p.grad(ut)
+    fe = p.eval(ut)
     p.sync()
     assert rel_scalar(f.item(), f_ref) <= TOL["f32"]
+    assert rel_scalar(fe.item(), f_ref) <= TOL["f32"]
     assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("box", [(1, 1, 1), (3, 5, 2), (9, 7, 5), (41, 3, 2)])
+def test_f32_forward_ragged_counts(api, box):
+    # element counts around and between the forward kernels' 256 / 512 element steps
+    mesh = W.tet_mesh(*box, jitter_seed=2, perm_seed=sum(box))
+    u = f32_round(np.random.default_rng(sum(box)).uniform(-1, 1, mesh.nv))
+    G32 = f32_round(mesh.G)
+    p = api.TetEnergy(torch.tensor(mesh.conn, device="cuda"),
+                      torch.tensor(G32, dtype=torch.float32, device="cuda"), mesh.nv, mode="recompute")
+    fe = p.eval(torch.tensor(u, dtype=torch.float32, device="cuda"))
+    p.sync()
+    assert rel_scalar(fe.item(), O.tet_value(mesh.conn, G32, u)) <= TOL["f32"]
 
 
 @pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
