@@ -294,6 +294,105 @@ __global__ void pair_split_vec_kernel(const double* __restrict__ u, const double
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_error(err, ERRBIT_RANGE);
 }
 
+// FP64 kernels in float pairs without shared-memory staging (the forward is
+// latency-bound on its gathers, and the staged tiles cap the SM at 3 CTAs):
+// one element per thread per step, G read from its prepared float-pair copy
+// in global memory, lanes of a warp on consecutive elements (warp-uniform
+// trip count, so the warp combine can run).  GRAD and HVP read u (and v) as
+// float pairs split once per call.
+template <int MODE, bool WARPC>
+__global__ void __launch_bounds__(TS_THREADS) tet_direct_pair_kernel(TsArgs<double> a) {
+  __shared__ float4 tab[kLogTableSize];
+  __shared__ double red[2 * TS_WARPS];
+  constexpr bool REV = MODE == TS_GRAD || MODE == TS_HVP;
+  constexpr bool USPLIT = REV;
+  for (int i = threadIdx.x; i < kLogTableSize; i += blockDim.x) tab[i] = a.logtab[i];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  bool bad = false;
+  Pair fb2{2.0f, 0.0f};
+  if constexpr (REV) {
+    const double fb = load_seed(a.seed);
+    bad |= !pair_in_range(2.0 * fb);
+    fb2 = split_f64(2.0 * fb);
+  }
+  Acc fa = acc_zero();
+  int cnt = 0;
+  const double* Gp = reinterpret_cast<const double*>(a.G);
+  const double* u = reinterpret_cast<const double*>(a.u);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < a.ne;
+       base += stride, ++cnt) {
+    const int64_t e = base + lane;
+    const bool act = e < a.ne;
+    const int4 c = act ? __ldcs(a.conn + e) : make_int4(-1, -1, -1, -1);
+    double wv[4];
+    Pair wp[4];
+    if (act) {
+      auto run = [&](const auto& sink) {
+        if constexpr (MODE == TS_HVP)
+          elem_pair_hvp<std::decay_t<decltype(sink)>, true, true>(
+              c, Gp + e * 12, u, reinterpret_cast<const double*>(a.v), fb2, sink, bad);
+        else
+          elem_pair<MODE, std::decay_t<decltype(sink)>, true, USPLIT>(
+              c, Gp + e * 12, u, fb2, tab, a.K, fa, sink, reinterpret_cast<double*>(a.tape) + e * 4,
+              bad);
+      };
+      if constexpr (WARPC) run(CollectSink<double>{wv, wp});
+      else run(AtomicSink<double>{reinterpret_cast<double*>(a.gu)});
+    }
+    if ((cnt & 31) == 31) acc_renorm(fa);
+    if constexpr (WARPC) {
+      const int key[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        warp_combine(act, key[k], Acc{wp[k].h, wp[k].l}, [](Acc x, Acc y) { return acc_add(x, y); },
+                     [&](int vtx, Acc tot) {
+                       atomicAdd(reinterpret_cast<double*>(a.gu) + vtx, pair_to_double_fast(acc_pair(tot)));
+                     });
+    }
+  }
+  if (bad) set_error(a.err, ERRBIT_RANGE);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fa = acc_add(fa, shfl_xor_acc2(fa, o));
+  Acc* ra = reinterpret_cast<Acc*>(red);
+  if (lane == 0) ra[warp] = fa;
+  __syncthreads();
+  Acc tot = acc_zero();
+  for (int w = 0; w < TS_WARPS; ++w) tot = acc_add(tot, ra[w]);
+  __syncthreads();
+  finish_sum<double>(acc_to_double(tot), a.fpart, a.counter, reinterpret_cast<double*>(a.f), 0, red);
+}
+
+template <int MODE, bool WARPC>
+static cudaError_t launch_direct_pair(const kg_problem* p, const TsArgs<double>& a, cudaStream_t s) {
+  static int occ = 0;
+  if (occ < 1) {
+    int o = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, tet_direct_pair_kernel<MODE, WARPC>,
+                                                      TS_THREADS, 0) != cudaSuccess)
+      o = 1;
+    occ = std::max(o, 1);
+  }
+  const int64_t g = std::min<int64_t>({(p->m + TS_THREADS - 1) / TS_THREADS,
+                                       (int64_t)num_sms() * occ, (int64_t)p->fpart_len});
+  tet_direct_pair_kernel<MODE, WARPC><<<(int)std::max<int64_t>(g, 1), TS_THREADS, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch_direct_pair(const kg_problem* p, int mode, const TsArgs<double>& a,
+                                        cudaStream_t s) {
+  const bool warp = p->strategy == KG_STRATEGY_WARP;
+  switch (mode) {
+    case TS_EVAL: return launch_direct_pair<TS_EVAL, false>(p, a, s);
+    case TS_TAPE: return launch_direct_pair<TS_TAPE, false>(p, a, s);
+    case TS_GRAD: return warp ? launch_direct_pair<TS_GRAD, true>(p, a, s)
+                              : launch_direct_pair<TS_GRAD, false>(p, a, s);
+    default: return warp ? launch_direct_pair<TS_HVP, true>(p, a, s)
+                         : launch_direct_pair<TS_HVP, false>(p, a, s);
+  }
+}
+
 // ---------------------------------------------------------------- host ----
 static float4* g_logtab[64] = {nullptr};
 static std::mutex g_logtab_mu;
@@ -463,6 +562,19 @@ static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, v
       if (e != cudaSuccess) return cuda_fail(e, "split vertex values");
       a.u = reinterpret_cast<const T*>(us);
       a.v = v ? reinterpret_cast<const T*>(us + p->n) : nullptr;
+    }
+  }
+  // float pairs from the prepared G, no bounds checks, any strategy but the shared-memory
+  // table: the direct kernels
+  if constexpr (sizeof(T) == 8) {
+    if (p->arith == KG_ARITH_PAIR && p->aprep && !p->opt.check && p->strategy != KG_STRATEGY_SHARED) {
+      static const char* dnames[4] = {"tet_direct_pair_kernel<eval>", "tet_direct_pair_kernel<grad>",
+                                      "tet_direct_pair_kernel<tape>", "tet_direct_pair_kernel<hvp>"};
+      prof_begin(s, dnames[mode]);
+      cudaError_t e = dispatch_direct_pair(p, mode, a, s);
+      prof_end(s);
+      count_launch();
+      return e == cudaSuccess ? KG_OK : cuda_fail(e, dnames[mode]);
     }
   }
   static const char* names[4] = {"tet_staged_kernel<eval>", "tet_staged_kernel<grad>",
