@@ -11,6 +11,10 @@
 // rescheduling proposed in Sec. 5).  In TAPE mode the forward stores c_e (for
 // fbar = 1) so that the reverse pass reads neither G nor u (Sec. 5, taping
 // allocated once outside the kernel).
+//
+// This file holds the set-up (validation, CSR build, prepared copies), the
+// tape scatter and CSR gather kernels, the direct FP32 kernels and the
+// dispatch; the FP64 and staged kernels are in tet_pair.cu.
 #include <cuda_runtime.h>
 
 #include <algorithm>

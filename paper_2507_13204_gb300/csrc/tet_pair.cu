@@ -1,6 +1,16 @@
-// Tet-mesh energy kernels with shared-memory staging of the element data.
+// Tet-mesh energy kernels for FP64 data and the staged variants.
 //
-// Each CTA walks tiles of 256 elements (tile = blockIdx.x, + gridDim.x, ...).
+// Which kernel runs:
+//   - FP64 in float pairs from the prepared G (the default), without bounds
+//     checks, any strategy but SHARED: tet_direct_pair_kernel, one element per
+//     thread per step with G read straight from global memory (the forward is
+//     latency-bound on its gathers; staging would cap occupancy);
+//   - FP32 without bounds checks, any strategy but SHARED: the direct FP32
+//     kernel in tet.cu;
+//   - everything else (native FP64, bounds checks, the SHARED strategy, pair
+//     arithmetic without a prepared G): tet_staged_kernel below.
+//
+// tet_staged_kernel: each CTA walks tiles of 256 elements (tile = blockIdx.x, + gridDim.x, ...).
 // Thread 0 streams each tile's connectivity (int4 per element) and G_e
 // (12 values per element) into a shared-memory ring (3 stages FP32, 2 FP64) with TMA bulk
 // copies (cp.async.bulk, mbarrier transaction counts); warps release a stage
