@@ -243,6 +243,9 @@ static kg_status lap_grad_t(kg_problem* p, const void* xv, void* f, void* gx, vo
   T* w = static_cast<T*>(p->y);
   T *x3 = w, *y = w + n, *y2 = w + 2 * n, *y2b = w + 3 * n, *yb = w + 4 * n, *x3b = w + 5 * n;
   // shadows start at zero (Sec. 3.1: the shadow of a constructed view)
+  // timed as one unit: the generated gradient's six kernels and the shadow zeroing
+  prof_begin(s, "lap generated gradient (memset + 6 kernels)");
+  struct End { cudaStream_t s; ~End() { prof_end(s); } } end{s};
   if ((e = cudaMemsetAsync(y2b, 0, sizeof(T) * 3 * (size_t)n, s)) != cudaSuccess)
     return cuda_fail(e, "zero shadows");
   lap_k1_scale<T><<<g, 256, 0, s>>>(x, x3, n);
