@@ -130,6 +130,18 @@ __host__ __device__ __forceinline__ void acc_fma(Acc& c, float ah, float al, flo
   c.l += r + e;
 }
 
+// The first term of an accumulation: (ah + al) * (bh + bl) as an
+// accumulator, the value acc_fma gives on a zero accumulator (up to the sign
+// of a zero) without its TwoSum, which the compiler cannot drop because
+// 0 + p is not p for p = -0.
+__host__ __device__ __forceinline__ Acc acc_prod(float ah, float al, float bh, float bl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  return Acc{p, e};
+}
+
 // Renormalise: move l into s so that |l| <= ulp(s)/2 again (TwoSum).  Long
 // accumulations call this every few terms; otherwise |l| grows with the
 // number of terms and its own float rounding becomes visible (n * 2^-48).

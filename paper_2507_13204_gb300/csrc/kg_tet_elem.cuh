@@ -72,46 +72,55 @@ __device__ __forceinline__ void sink_pair(const CollectSink<T>& gu, int k, int, 
   gu.prs[k] = c;
 }
 
-// Warp-level combine of one contribution per lane: lanes whose key (vertex)
-// is equal form a group (match.any), and the lowest lane of each group adds
-// the group total to gu with one atomic.  Inactive lanes take part in the
-// shuffles only.  All 32 lanes must call it together.
-//   - float-pair or FP64 values (an add costs ~10 instructions or the FP64
-//     unit), every group a contiguous
-//     run of lanes (elements numbered along the mesh): a segmented suffix
-//     scan, ceil(log2 of the longest run) steps of shift-down adds that stay
-//     inside the run;
-//   - otherwise: every lane walks the group members above it, one shuffle
-//     round per member (for plain floats this is cheaper than the extra votes
-//     the scan needs).
+// Warp-level combine of one contribution per lane: a run of consecutive lanes
+// whose keys (vertices) are equal adds its values with a segmented suffix
+// scan (ceil(log2 of the longest run) shift-down steps that stay inside the
+// run), and the run's first lane adds the total to gu with one atomic.  Equal
+// keys that are not adjacent form separate runs and simply issue separate
+// atomics, so the result does not depend on the element order; elements
+// numbered along the mesh put the shared vertices of neighbouring elements
+// in neighbouring lanes.  Inactive lanes take part in the shuffles only.
+// All 32 lanes must call it together.
 template <typename V, typename AddF, typename FlushF>
 __device__ __forceinline__ void warp_combine(bool active, int key, V val, AddF add, FlushF flush) {
   const int lane = threadIdx.x & 31;
-  const unsigned peers = __match_any_sync(0xffffffffu, active ? key : -1);
-  const int first = __ffs(peers) - 1, last = 31 - __clz(peers);
-  const unsigned run = (last == 31 ? 0xFFFFFFFFu : ((2u << last) - 1u)) & ~((1u << first) - 1u);
+  const int k = active ? key : -1;
+  const int up = __shfl_up_sync(0xffffffffu, k, 1);
+  const unsigned heads = __ballot_sync(0xffffffffu, lane == 0 || up != k);
+  const unsigned above = heads & (0xFFFFFFFEu << lane);  // heads of the runs after this lane's
+  const int last = above ? __ffs(above) - 2 : 31;        // last lane of this lane's run
+  const int span = (int)__reduce_max_sync(0xffffffffu, (unsigned)(last - lane + 1));
   V acc = val;
-  constexpr bool kScan = !std::is_same<V, float>::value;  // pairs and FP64 adds
-  if (kScan && __all_sync(0xffffffffu, peers == run)) {
-    const int span = (int)__reduce_max_sync(0xffffffffu, (unsigned)(last - first + 1));
-    for (int d = 1; d < span; d <<= 1) {
-      const V other = shfl_down_v(acc, d);
-      if (lane + d <= last) acc = add(acc, other);
-    }
-  } else {
-    unsigned rest = active ? peers & (0xFFFFFFFEu << lane) : 0u;
-    // rounds = the largest group's size - 1, from one reduction instead of a vote per round
-    const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(rest));
-    for (int r = 0; r < rounds; ++r) {
-      const int src = rest ? __ffs(rest) - 1 : lane;
-      const V other = shfl_v(val, src);
-      if (rest) {
-        acc = add(acc, other);
-        rest &= rest - 1u;
-      }
+  for (int d = 1; d < span; d <<= 1) {
+    const V other = shfl_down_v(acc, d);
+    if (lane + d <= last) acc = add(acc, other);
+  }
+  if (active && ((heads >> lane) & 1u)) flush(key, acc);
+}
+
+// The same combine by key groups instead of runs, for plain float values:
+// lanes with equal keys anywhere in the warp find each other with match.any,
+// and every lane walks the group members above it, one shuffle round per
+// member (rounds = the largest group's size - 1).  It catches equal keys that
+// are not adjacent, so it issues fewer atomics than warp_combine, at the cost
+// of the match and of more rounds; it also needs fewer registers, which keeps
+// the FP32 direct kernels at four blocks of 256 threads per SM.
+__device__ __forceinline__ void warp_combine_groups(bool active, int key, float val,
+                                                    float* __restrict__ gu) {
+  const int lane = threadIdx.x & 31;
+  const unsigned peers = __match_any_sync(0xffffffffu, active ? key : -1);
+  unsigned rest = active ? peers & (0xFFFFFFFEu << lane) : 0u;
+  const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)__popc(rest));
+  float acc = val;
+  for (int r = 0; r < rounds; ++r) {
+    const int src = rest ? __ffs(rest) - 1 : lane;
+    const float other = __shfl_sync(0xffffffffu, val, src);
+    if (rest) {
+      acc += other;
+      rest &= rest - 1u;
     }
   }
-  if (active && lane == first) flush(key, acc);
+  if (active && lane == __ffs(peers) - 1) atomicAdd(gu + key, acc);
 }
 
 // Per-tile table of (vertex, partial sum) in shared memory.  keys[] holds -1
@@ -249,14 +258,14 @@ __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict
   Pair g[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    Acc a = acc_zero();
+    Acc a = acc_prod(G[4 * r].h, G[4 * r].l, U[0].h, U[0].l);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, U[k].h, U[k].l);
+    for (int k = 1; k < 4; ++k) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, U[k].h, U[k].l);
     g[r] = acc_pair(a);
   }
-  Acc sa = acc_zero();
+  Acc sa = acc_prod(g[0].h, g[0].l, g[0].h, g[0].l);
 #pragma unroll
-  for (int r = 0; r < 3; ++r) acc_fma(sa, g[r].h, g[r].l, g[r].h, g[r].l);
+  for (int r = 1; r < 3; ++r) acc_fma(sa, g[r].h, g[r].l, g[r].h, g[r].l);
   const Pair s = acc_pair(sa);
   Pair t;
   const Pair lf = pair_log1p(s, tab, K, t);
@@ -269,9 +278,9 @@ __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict
     Pair cp[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-      Acc a = acc_zero();
+      Acc a = acc_prod(G[k].h, G[k].l, wg[0].h, wg[0].l);
 #pragma unroll
-      for (int r = 0; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, wg[r].h, wg[r].l);
+      for (int r = 1; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, wg[r].h, wg[r].l);
       cp[k] = acc_pair(a);
     }
     if constexpr (MODE == TS_GRAD) {
@@ -360,18 +369,20 @@ __device__ __forceinline__ void elem_pair_hvp(const int4 c, const double* __rest
   Pair g[3], gd[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
-    Acc a = acc_zero(), b = acc_zero();
+    Acc a = acc_prod(G[4 * r].h, G[4 * r].l, U[0].h, U[0].l);
+    Acc b = acc_prod(G[4 * r].h, G[4 * r].l, V[0].h, V[0].l);
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 1; k < 4; ++k) {
       acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, U[k].h, U[k].l);
       acc_fma(b, G[4 * r + k].h, G[4 * r + k].l, V[k].h, V[k].l);
     }
     g[r] = acc_pair(a);
     gd[r] = acc_pair(b);
   }
-  Acc sa = acc_zero(), sda = acc_zero();
+  Acc sa = acc_prod(g[0].h, g[0].l, g[0].h, g[0].l);
+  Acc sda = acc_prod(g[0].h, g[0].l, gd[0].h, gd[0].l);
 #pragma unroll
-  for (int r = 0; r < 3; ++r) {
+  for (int r = 1; r < 3; ++r) {
     acc_fma(sa, g[r].h, g[r].l, g[r].h, g[r].l);
     acc_fma(sda, g[r].h, g[r].l, gd[r].h, gd[r].l);
   }
@@ -389,9 +400,9 @@ __device__ __forceinline__ void elem_pair_hvp(const int4 c, const double* __rest
   for (int r = 0; r < 3; ++r) h[r] = pair_add(pair_mul(wd, g[r]), pair_mul(w, gd[r]));
 #pragma unroll
   for (int k = 0; k < 4; ++k) {
-    Acc a = acc_zero();
+    Acc a = acc_prod(G[k].h, G[k].l, h[0].h, h[0].l);
 #pragma unroll
-    for (int r = 0; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, h[r].h, h[r].l);
+    for (int r = 1; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, h[r].h, h[r].l);
     sink_pair(gu, k, idx[k], acc_pair(a));
   }
 }

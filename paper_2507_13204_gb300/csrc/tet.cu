@@ -66,12 +66,13 @@ __global__ void __launch_bounds__(256) tet_tape_scatter_kernel(const int4* __res
   }
 }
 
-// FP32 kernels without shared-memory staging (the staged kernel's tiles are
-// limited by shared memory to 4 CTAs per SM; these run 6).  Each thread takes
-// two elements per step: their conn (int4) and G (three float4) are streamed
-// with no L1 allocation and all of their loads and u (and v) gathers are
-// issued before any is used.  Lanes of a warp hold consecutive elements, so
-// the warp combine of the scatter sees the mesh order.  Modes as the staged
+// FP32 kernels without shared-memory staging: no ring, no CTA barrier per
+// tile, and more loads in flight per warp than the staged kernel at the same
+// four CTAs of 256 threads per SM.  Each thread takes two elements per step:
+// their conn (int4) and G (three float4) are streamed with no L1 allocation
+// and all of their loads and u (and v) gathers are issued before any is used.
+// Lanes of a warp hold consecutive elements; the scatter combines equal
+// vertices of a warp by key groups (warp_combine_groups).  Modes as the staged
 // kernel: forward, gradient (warp-combined or plain atomics), tape, Hessian-
 // vector product.
 struct DirectArgs {
@@ -168,8 +169,7 @@ __global__ void __launch_bounds__(256) tet_direct_f32_kernel(DirectArgs a) {
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
             if constexpr (WARPC) {
-              warp_combine(act[h], key[k], cv[k], [](float x, float y) { return x + y; },
-                           [&](int vtx, float tot) { atomicAdd(a.gu + vtx, tot); });
+              warp_combine_groups(act[h], key[k], cv[k], a.gu);
             } else if (act[h]) {
               atomicAdd(a.gu + key[k], cv[k]);
             }

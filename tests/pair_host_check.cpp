@@ -90,5 +90,19 @@ int main() {
   }
   printf("pair_log1p %.6Lg\n", w_log);
   printf("pair_log1p_t %.6Lg\n", w_t);
+
+  // acc_prod: the same accumulator as acc_fma on a zero accumulator
+  long double w_prod = 0;
+  for (int i = 0; i < 1000000; ++i) {
+    float ah, al, bh, bl;
+    split_ld((long double)U(g) * mag(-30, 30), ah, al);
+    split_ld((long double)U(g) * mag(-30, 30), bh, bl);
+    const kg::Acc p = kg::acc_prod(ah, al, bh, bl);
+    kg::Acc q = kg::acc_zero();
+    kg::acc_fma(q, ah, al, bh, bl);
+    const long double d = std::fabs((long double)p.s - q.s) + std::fabs((long double)p.l - q.l);
+    if (d > w_prod) w_prod = d;
+  }
+  printf("acc_prod_vs_acc_fma %.6Lg\n", w_prod);
   return 0;
 }

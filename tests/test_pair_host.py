@@ -1,7 +1,8 @@
 """The float-pair helpers of the FP64 kernels (kg_pair.cuh), compiled for the host
 with g++ and checked against long double arithmetic on seeded random inputs:
 split of a double, pair -> double conversion, exact float -> double, pair
-reciprocal and pair log1p."""
+reciprocal and pair log1p; and that a chain started with acc_prod holds exactly
+what acc_fma on a zero accumulator gives."""
 import os
 import shutil
 import subprocess
@@ -19,6 +20,7 @@ BOUNDS = {
     "pair_recip": 2.0 ** -45,
     "pair_log1p": 2.0 ** -44,
     "pair_log1p_t": 2.0 ** -46,
+    "acc_prod_vs_acc_fma": 0.0,
 }
 
 
