@@ -303,3 +303,29 @@ def test_warp_combine_on_a_mesh_where_every_tet_shares_one_vertex(api):
         tol = TOL["f64"] if dtype == torch.float64 else TOL["f32"]
         assert rel_scalar(f.item(), f_ref) <= tol
         assert rel_l2(g.cpu().numpy(), g_ref) <= tol
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_warp_combine_odd_counts_and_repeated_elements(api, dtype):
+    # odd element counts around the 32-lane warp (a last warp with only some lanes active)
+    # and a mesh where every element appears twice in a row (neighbouring lanes hold the
+    # same four vertices: every slot a group or run of two), for the gradient and H v
+    mesh = W.tet_mesh(6, 5, 4, jitter_seed=2, perm_seed=5)
+    rng = np.random.default_rng(31)
+    rnd = (lambda a: a) if dtype == torch.float64 else f32_round
+    tol = TOL["f64"] if dtype == torch.float64 else TOL["f32"]
+    u, v = rnd(rng.uniform(-1, 1, mesh.nv)), rnd(rng.uniform(-1, 1, mesh.nv))
+    cases = [np.arange(ne) for ne in (1, 3, 63, 65, 129, 701)] + [np.repeat(np.arange(333), 2)]
+    for rows in cases:
+        conn, G = np.ascontiguousarray(mesh.conn[rows]), rnd(np.ascontiguousarray(mesh.G[rows]))
+        f_ref, g_ref = O.tet_grad(conn, G, u)
+        h_ref = O.tet_hvp(conn, G, u, v)
+        p = api.TetEnergy(torch.tensor(conn, device="cuda"), torch.tensor(G, dtype=dtype, device="cuda"),
+                          mesh.nv, strategy="warp")
+        ut = torch.tensor(u, dtype=dtype, device="cuda")
+        f, g = p.grad(ut)
+        hv = p.hvp(ut, torch.tensor(v, dtype=dtype, device="cuda"))
+        p.sync()
+        assert rel_scalar(f.item(), f_ref) <= tol, len(rows)
+        assert rel_l2(g.cpu().numpy(), g_ref) <= tol, len(rows)
+        assert rel_l2(hv.cpu().numpy(), h_ref) <= tol, len(rows)
