@@ -347,11 +347,11 @@ __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, co
         warp_combine(act, key[k], Acc{cpr[k].h, cpr[k].l},
                      [](Acc x, Acc y) { return acc_add(x, y); },
                      [&](int v, Acc tot) {
-                       atomicAdd(reinterpret_cast<double*>(gu) + v, pair_to_double_fast(acc_pair(tot)));
+                       red_add(reinterpret_cast<double*>(gu) + v, pair_to_double_fast(acc_pair(tot)));
                      });
       } else {
         warp_combine(act, key[k], cv[k], [](T x, T y) { return x + y; },
-                     [&](int v, T tot) { atomicAdd(gu + v, tot); });
+                     [&](int v, T tot) { red_add(gu + v, tot); });
       }
     }
   }

@@ -50,7 +50,7 @@ __device__ __forceinline__ Acc shfl_down_v(Acc v, int d) {
 template <typename T>
 struct AtomicSink {
   T* gu;
-  __device__ __forceinline__ void operator()(int, int v, T c) const { atomicAdd(gu + v, c); }
+  __device__ __forceinline__ void operator()(int, int v, T c) const { red_add(gu + v, c); }
 };
 
 template <typename Sink>
@@ -120,7 +120,7 @@ __device__ __forceinline__ void warp_combine_groups(bool active, int key, float 
       rest &= rest - 1u;
     }
   }
-  if (active && lane == __ffs(peers) - 1) atomicAdd(gu + key, acc);
+  if (active && lane == __ffs(peers) - 1) red_add(gu + key, acc);
 }
 
 // Per-tile table of (vertex, partial sum) in shared memory.  keys[] holds -1
@@ -146,7 +146,7 @@ struct HashSink {
       }
       h = (h + 1) & (SLOTS - 1);
     }
-    atomicAdd(gu + v, c);
+    red_add(gu + v, c);
   }
 };
 
@@ -158,7 +158,7 @@ __device__ __forceinline__ void hash_flush(int* keys, T* vals, T* gu, int tid) {
   for (int j = tid; j < SLOTS; j += THREADS) {
     const int k = keys[j];
     if (k != -1) {
-      atomicAdd(gu + k, vals[j]);
+      red_add(gu + k, vals[j]);
       keys[j] = -1;
       vals[j] = T(0);
     }

@@ -165,10 +165,10 @@ __global__ void lap_k2t_stencil(const T* y, T* y2b, T* yb, T* x3b, T* gb, int n,
     y2b[j] -= r;
     yb[j] += T(2) * y[j] * r;
     const T ry = yb[j];
-    if (j != n - 1) atomicAdd(x3b + j + 1, -ry);
-    if (j != 0) atomicAdd(x3b + j - 1, -ry);
+    if (j != n - 1) red_add(x3b + j + 1, -ry);
+    if (j != 0) red_add(x3b + j - 1, -ry);
     yb[j] -= ry;
-    atomicAdd(x3b + j, T(2) * ry);
+    red_add(x3b + j, T(2) * ry);
     if (gb) gb[j] = accumulate ? gb[j] - ry : -ry;
   }
 }

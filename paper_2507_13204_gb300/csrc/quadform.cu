@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(512) qf_team_kernel(QfArgs<T> a) {
 }
 
 // Reverse with the forward schedule (the paper's atomic scatter): each team
-// re-reads its row and issues atomicAdd(&gx[j], ybar_i A_ij); ybar_i comes from
+// re-reads its row and adds ybar_i A_ij into gx[j] (a global red); ybar_i comes from
 // the y the forward kernel stored.
 template <typename T, int TEAM, int CPT_MAX>
 __global__ void __launch_bounds__(512) qf_atomic_adjoint_kernel(QfArgs<T> a, T* gx) {
@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(512) qf_atomic_adjoint_kernel(QfArgs<T> a, T* 
 #pragma unroll
     for (int k = 0; k < CPT_MAX; ++k) {
       const int j = lt + k * TEAM;
-      if (k < a.cpt && j < n) atomicAdd(gx + j, yb * ld_stream(Ar + j));
+      if (k < a.cpt && j < n) red_add(gx + j, yb * ld_stream(Ar + j));
     }
   }
 }

@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(SQ_THREADS) spq_row_kernel(SqArgs<T> a) {
       for (int u = 0; u < SQ_U; ++u) {
         const int p = p0 + tl + u * TW;
         if (p < p1) {
-          if constexpr (MODE == SQ_ATOMIC) atomicAdd(a.gx + c[u], v[u] * yb);
+          if constexpr (MODE == SQ_ATOMIC) red_add(a.gx + c[u], v[u] * yb);
           if (a.gval) {
             const T g = xv[u] * yb;
             a.gval[p] = a.accumulate ? a.gval[p] + g : g;
@@ -127,7 +127,7 @@ __global__ void __launch_bounds__(SQ_THREADS) spq_row_kernel(SqArgs<T> a) {
       }
       for (int p = p0 + SQ_U * TW + tl; p < p1; p += TW) {
         const int cp = __ldg(a.col + p);
-        if constexpr (MODE == SQ_ATOMIC) atomicAdd(a.gx + cp, __ldg(a.val + p) * yb);
+        if constexpr (MODE == SQ_ATOMIC) red_add(a.gx + cp, __ldg(a.val + p) * yb);
         if (a.gval) {
           const T g = __ldg(a.x + cp) * yb;
           a.gval[p] = a.accumulate ? a.gval[p] + g : g;
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(SQ_THREADS) spq_row_pair_kernel(SqPairArgs a) 
           const int cp = __ldg(a.col + p);
           if constexpr (MODE == SQ_ATOMIC) {
             const float2 v = __ldg(a.valp + p);
-            atomicAdd(a.gx + cp, pair_to_double_fast(pair_mul(Pair{v.x, v.y}, yb)));
+            red_add(a.gx + cp, pair_to_double_fast(pair_mul(Pair{v.x, v.y}, yb)));
           }
           if (a.gval) {
             const double g = pair_to_double_fast(pair_mul(split_f64(__ldg(a.x + cp)), yb));

@@ -58,9 +58,9 @@ __global__ void __launch_bounds__(256) tet_tape_scatter_kernel(const int4* __res
     for (int k = 0; k < 4; ++k) {
       if constexpr (WARPC) {
         warp_combine(act, key[k], fb * t[k], [](T x, T y) { return x + y; },
-                     [&](int v, T tot) { atomicAdd(gu + v, tot); });
+                     [&](int v, T tot) { red_add(gu + v, tot); });
       } else if (act) {
-        atomicAdd(gu + key[k], fb * t[k]);
+        red_add(gu + key[k], fb * t[k]);
       }
     }
   }
@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(256) tet_direct_f32_kernel(DirectArgs a) {
             if constexpr (WARPC) {
               warp_combine_groups(act[h], key[k], cv[k], a.gu);
             } else if (act[h]) {
-              atomicAdd(a.gu + key[k], cv[k]);
+              red_add(a.gu + key[k], cv[k]);
             }
           }
         }

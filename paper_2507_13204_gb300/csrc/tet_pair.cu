@@ -224,12 +224,12 @@ __global__ void __launch_bounds__(TS_THREADS) tet_staged_kernel(TsArgs<T> a) {
           warp_combine(wact, key[k], Acc{wp[k].h, wp[k].l},
                        [](Acc x, Acc y) { return acc_add(x, y); },
                        [&](int v, Acc tot) {
-                         atomicAdd(reinterpret_cast<double*>(a.gu) + v,
+                         red_add(reinterpret_cast<double*>(a.gu) + v,
                                    pair_to_double_fast(acc_pair(tot)));
                        });
         } else {
           warp_combine(wact, key[k], wv[k], [](T x, T y) { return x + y; },
-                       [&](int v, T tot) { atomicAdd(a.gu + v, tot); });
+                       [&](int v, T tot) { red_add(a.gu + v, tot); });
         }
       }
     }
@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(TS_THREADS) tet_direct_pair_kernel(TsArgs<doub
       for (int k = 0; k < 4; ++k)
         warp_combine(act, key[k], Acc{wp[k].h, wp[k].l}, [](Acc x, Acc y) { return acc_add(x, y); },
                      [&](int vtx, Acc tot) {
-                       atomicAdd(reinterpret_cast<double*>(a.gu) + vtx, pair_to_double_fast(acc_pair(tot)));
+                       red_add(reinterpret_cast<double*>(a.gu) + vtx, pair_to_double_fast(acc_pair(tot)));
                      });
     }
   }
