@@ -711,14 +711,14 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
 # fingerprint it was taken with; after any change to them the field is null until re-measured.
 _CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_13204_gb300", "csrc")
 _TRAFFIC = {
-    ("dense", "f64"): (803419904, ["quadform_pair.cu", "kg_pair.cuh", "kg_device.cuh"],
-                       "3f7c7c2906658dbe"),
-    ("dense32", "f32"): (404314112, ["quadform_f32.cu", "kg_pair.cuh", "kg_device.cuh"],
-                         "5518370ce83051b3"),
-    ("tet", "f64"): (707723520, ["tet_pair.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
-                     "452fd2ebc35a5d87"),
-    ("tet32", "f32"): (394661120, ["tet.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
-                       "7ea154c8003ee969"),
+    ("dense", "f64"): (802733824, ["quadform_pair.cu", "kg_pair.cuh", "kg_device.cuh"],
+                       "da336917204c8c91"),
+    ("dense32", "f32"): (403951104, ["quadform_f32.cu", "kg_pair.cuh", "kg_device.cuh"],
+                         "6edb3d247cf29820"),
+    ("tet", "f64"): (708191488, ["tet_pair.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
+                     "625a64cbf275cc2f"),
+    ("tet32", "f32"): (394469120, ["tet.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
+                       "35bbbb14f0d70488"),
 }
 
 
