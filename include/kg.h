@@ -103,7 +103,9 @@ typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
  *   WARP      (tet) the forward schedule with the scatter-adds combined within
  *             each warp: lanes whose element shares a vertex (in the same local
  *             slot) add their values by shuffles and one lane issues the
- *             atomic.
+ *             atomic.  FP64 data combines runs of consecutive lanes (elements
+ *             numbered along the mesh); FP32 data combines equal vertices
+ *             anywhere in the warp.  The result holds for any element order.
  *   AUTO      FUSED for dense, WARP for tets, ATOMIC for sparse, the stencil
  *             transpose for 1-D. */
 typedef enum {

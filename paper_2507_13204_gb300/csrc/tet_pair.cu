@@ -28,11 +28,11 @@
 // 1024 contributions, so global atomics drop ~5x.
 //
 // KG_STRATEGY_WARP: the four contributions of each lane stay in registers;
-// per local vertex slot k, lanes of a warp holding the same global vertex
-// (match.any) add their values by shuffles (float pairs for FP64 data) and
-// the lowest lane of each group issues one atomic.  No shared memory and no
-// CTA barrier; on the Kuhn grid (six consecutive tets share the cube's
-// diagonal ends in slots 0 and 3) global atomics drop ~3x.
+// per local vertex slot k, consecutive lanes holding the same global vertex
+// add their values by a segmented scan in float pairs (warp_combine) and the
+// first lane of each run issues one global reduction.  No shared memory and
+// no CTA barrier; on the Kuhn grid (six consecutive tets share the cube's
+// diagonal ends in slots 0 and 3) global reductions drop ~2x.
 //
 // Arithmetic: FP32 for FP32 problems; for FP64 problems either native FP64
 // or float pairs (kg_pair.cuh) with the results converted back to double for

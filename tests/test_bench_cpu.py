@@ -26,7 +26,7 @@ def test_fingerprint_matches_when_sources_are_restored(tmp_path, monkeypatch):
     assert bench.recorded_traffic("dense", "f64", True) == nbytes
 
 
-def test_traffic_is_null_once_a_kernel_source_changes(tmp_path, monkeypatch):
+def test_traffic_is_null_once_a_kernel_source_changes_but_not_for_comments(tmp_path, monkeypatch):
     csrc = tmp_path / "csrc"
     shutil.copytree(bench._CSRC, csrc)
     monkeypatch.setattr(bench, "_CSRC", str(csrc))
@@ -35,7 +35,10 @@ def test_traffic_is_null_once_a_kernel_source_changes(tmp_path, monkeypatch):
     tb, tf, _ = bench._TRAFFIC[("dense32", "f32")]
     monkeypatch.setitem(bench._TRAFFIC, ("dense32", "f32"), (tb, tf, bench.source_fingerprint(tf)))
     assert bench.recorded_traffic("dense", "f64", True) == nbytes
+    with open(csrc / "quadform_pair.cu", "a") as fh:  # comments and blank lines: same code
+        fh.write("\n// edited\n/* a block\n   comment */\n\n")
+    assert bench.recorded_traffic("dense", "f64", True) == nbytes
     with open(csrc / "quadform_pair.cu", "a") as fh:
-        fh.write("\n// edited\n")
+        fh.write("\nstatic int edited_code = 1;\n")
     assert bench.recorded_traffic("dense", "f64", True) is None
     assert bench.recorded_traffic("dense32", "f32", True) == tb  # other sources untouched
