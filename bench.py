@@ -208,13 +208,13 @@ class DenseWL(Workload):
 class SparseWL(Workload):
     """Sparse ||Ax||^2, A 2^20 x 2^20 in CSR with 8..24 stored entries per row."""
 
-    def __init__(self, m, dtype, strategy="auto"):
+    def __init__(self, m, dtype, strategy="auto", arith="auto"):
         self.m = m
         self.dtype = dtype
         self.dtype_name = dtype
         self.es = 8 if dtype == "f64" else 4
         self.strategy = strategy
-        self.arith = "native"
+        self.arith = arith
 
     def setup(self, dev):
         import torch
@@ -229,7 +229,8 @@ class SparseWL(Workload):
         self.cl = torch.tensor(A.col, device=dev)
         self.vl = torch.tensor(A.val, dtype=td, device=dev)
         self.xt = torch.tensor(x, dtype=td, device=dev)
-        self.p = api.SpQuadForm(self.rp, self.cl, self.vl, self.n, strategy=self.strategy)
+        self.p = api.SpQuadForm(self.rp, self.cl, self.vl, self.n, strategy=self.strategy,
+                                arith=self.arith)
         self.gx = torch.empty(self.n, dtype=td, device=dev)
         self.f = torch.empty((), dtype=td, device=dev)
         self.fe = torch.empty((), dtype=td, device=dev)
@@ -694,7 +695,7 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
     if name == "hvp32":
         return HvpWL(size or 100, "f32", strategy=strategy or "auto")
     if name == "sparse":
-        return SparseWL(size or (1 << 20), "f64", strategy=strategy or "auto")
+        return SparseWL(size or (1 << 20), "f64", strategy=strategy or "auto", arith=arith)
     if name == "sparse32":
         return SparseWL(size or (1 << 20), "f32", strategy=strategy or "auto")
     if name == "laplace":
