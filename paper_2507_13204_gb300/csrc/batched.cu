@@ -11,8 +11,9 @@
 //   dense tile:  rows [r0, r0 + R): y_i by a row team (a warp for n <= 256,
 //                the CTA otherwise), ybar_i = 2 y_i, private xbar partial of
 //                the tile written to the instance's partial buffer;
-//   tet tile:    elements [e0, e0 + T): f_e and the scatter of c_e (warp-combined atomics)
-//                into gu (zeroed by a small kernel earlier in the graph).
+//   tet tile:    elements [e0, e0 + T): f_e and the scatter of c_e into gu (zeroed
+//                by a small kernel earlier in the graph): one global reduction per
+//                contribution, or warp-combined first with the WARP strategy.
 // The CTA that finishes an instance's last tile (a per-instance arrival
 // counter; nobody waits) sums the instance's partials in tile order into gx
 // and f, and resets the counter.  The last CTA to leave resets the queue head,
@@ -150,89 +151,114 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
   Acc fp = acc_zero();
   FSum<T> fn;
   const int64_t r1 = w.start + w.count;
-  const int iters = (w.count + NT - 1) / NT;
-  // software pipeline: the next row's loads are in flight while this row computes
-  T an[B_CPT];
-  auto load_row = [&](int itr_, T* dst) {
-    const int64_t r = w.start + (int64_t)itr_ * NT + team;
-    const bool v = itr_ < iters && r < r1;
-    const T* Ar = A + (v ? r : w.start) * (int64_t)n;
+  if constexpr (PAIR) {
+    // Two rows per team and iteration, rows r and r + NT: their loads are issued
+    // together, and one transposed butterfly reduces both dot products (the
+    // first exchange hands each half of the team one row), so the reduction
+    // and, for teams wider than a warp, the barrier are paid once per two rows.
+    constexpr int W = TEAM < 32 ? TEAM : 32;  // lanes of the team inside one warp
+    const bool upper = (lane & (W / 2)) != 0;  // keeps the second row
+    const int iters2 = (w.count + 2 * NT - 1) / (2 * NT);
+    for (int itr = 0; itr < iters2; ++itr) {
+      const int64_t rr[2] = {w.start + (int64_t)itr * 2 * NT + team,
+                             w.start + (int64_t)itr * 2 * NT + NT + team};
+      const bool vr[2] = {rr[0] < r1, rr[1] < r1};
+      float ah[2][B_CPT], al[2][B_CPT];
 #pragma unroll
-    for (int k = 0; k < B_CPT; ++k) {
-      const int j = lt + k * TEAM;
-      dst[k] = (k < cpt && v && j < n) ? __ldcs(Ar + j) : T(0);
-    }
-  };
-  load_row(0, an);
-  for (int itr = 0; itr < iters; ++itr) {
-    const int64_t r = w.start + (int64_t)itr * NT + team;
-    const bool valid = r < r1;
-    float ah[B_CPT], al[B_CPT];
-    T av[B_CPT];
+      for (int q = 0; q < 2; ++q) {
+        const T* Ar = A + (vr[q] ? rr[q] : w.start) * (int64_t)n;
 #pragma unroll
-    for (int k = 0; k < B_CPT; ++k) av[k] = an[k];
-    load_row(itr + 1, an);
-#pragma unroll
-    for (int k = 0; k < B_CPT; ++k) {
-      if constexpr (PAIR) {
-        if (k < cpt) b_split<PAIR, T, PREP>(av[k], ah[k], al[k]);
-        else ah[k] = al[k] = 0.f;
-      }
-    }
-    if constexpr (PAIR) {
-      Acc y0 = acc_zero(), y1 = acc_zero();
-#pragma unroll
-      for (int k = 0; k < B_CPT; k += 2) {
-        if (k < cpt) acc_fma(y0, ah[k], al[k], xh[k], xl[k]);
-        if (k + 1 < cpt) acc_fma(y1, ah[k + 1], al[k + 1], xh[k + 1], xl[k + 1]);
-      }
-      Acc yv = acc_add(y0, y1);
-#pragma unroll
-      for (int o = (TEAM < 32 ? TEAM : 32) / 2; o > 0; o >>= 1) yv = acc_add(yv, shfl_xor_acc2(yv, o));
-      if constexpr (TEAM > 32) {  // warps of the team exchange through shared memory
-        constexpr int TW = TEAM / 32;
-        Acc* ra = reinterpret_cast<Acc*>(red) + (itr & 1) * BW + team * TW;
-        if (lane == 0) ra[warp % TW] = yv;
-        team_barrier<TEAM>(team);
-        yv = ra[0];
-#pragma unroll
-        for (int q = 1; q < TW; ++q) yv = acc_add(yv, ra[q]);
-      }
-      if (valid) {
-        const Pair y = acc_pair(yv);
-        const Pair y2 = pair_mul(y, y);
-        fp = acc_add(fp, Acc{y2.h, y2.l});
-        const Pair yb{2.0f * y.h, 2.0f * y.l};  // exact
-#pragma unroll
-        for (int k = 0; k < B_CPT; ++k)
-          if (k < cpt) acc_fma(xbp[k], ah[k], al[k], yb.h, yb.l);
-        if ((itr & 15) == 15) {
-#pragma unroll
-          for (int k = 0; k < B_CPT; ++k) acc_renorm(xbp[k]);
+        for (int k = 0; k < B_CPT; ++k) {
+          const int j = lt + k * TEAM;
+          const T v = (k < cpt && vr[q] && j < n) ? __ldcs(Ar + j) : T(0);
+          b_split<PAIR, T, PREP>(v, ah[q][k], al[q][k]);
         }
       }
-    } else {
-      T d = T(0);
+      Acc y[2] = {acc_zero(), acc_zero()};
 #pragma unroll
-      for (int k = 0; k < B_CPT; ++k)
-        if (k < cpt) d = fma(av[k], xv[k], d);
-#pragma unroll
-      for (int o = (TEAM < 32 ? TEAM : 32) / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if constexpr (TEAM > 32) {
-        constexpr int TW = TEAM / 32;
-        T* rt = reinterpret_cast<T*>(red) + (itr & 1) * BW + team * TW;
-        if (lane == 0) rt[warp % TW] = d;
-        team_barrier<TEAM>(team);
-        d = rt[0];
-#pragma unroll
-        for (int q = 1; q < TW; ++q) d += rt[q];
+      for (int k = 0; k < B_CPT; ++k) {
+        if (k < cpt) {
+          acc_fma(y[0], ah[0][k], al[0][k], xh[k], xl[k]);
+          acc_fma(y[1], ah[1][k], al[1][k], xh[k], xl[k]);
+        }
       }
-      if (valid) {
-        fn.add(d);
-        const T yb = T(2) * d;
+      Acc keep = upper ? y[1] : y[0];
+      keep = acc_add(keep, shfl_xor_acc2(upper ? y[0] : y[1], W / 2));
+#pragma unroll
+      for (int o = W / 4; o > 0; o >>= 1) keep = acc_add(keep, shfl_xor_acc2(keep, o));
+      if constexpr (TEAM > 32) {  // warps of the team exchange through shared memory
+        constexpr int TW = TEAM / 32;
+        Acc* ra = reinterpret_cast<Acc*>(red) + (itr & 1) * 2 * BW + team * 2 * TW;  // [TW][2]
+        if ((lane & (W / 2 - 1)) == 0) ra[(warp % TW) * 2 + (upper ? 1 : 0)] = keep;
+        team_barrier<TEAM>(team);
+        keep = ra[upper ? 1 : 0];
+#pragma unroll
+        for (int q = 1; q < TW; ++q) keep = acc_add(keep, ra[q * 2 + (upper ? 1 : 0)]);
+      }
+      const Acc other = shfl_xor_acc2(keep, W / 2);
+      const Acc yt[2] = {upper ? other : keep, upper ? keep : other};
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        if (vr[q]) {
+          const Pair yq = acc_pair(yt[q]);
+          const Pair y2 = pair_mul(yq, yq);
+          fp = acc_add(fp, Acc{y2.h, y2.l});
+          const Pair yb{2.0f * yq.h, 2.0f * yq.l};  // exact
+#pragma unroll
+          for (int k = 0; k < B_CPT; ++k)
+            if (k < cpt) acc_fma(xbp[k], ah[q][k], al[q][k], yb.h, yb.l);
+        }
+      }
+      if ((itr & 7) == 7) {
+#pragma unroll
+        for (int k = 0; k < B_CPT; ++k) acc_renorm(xbp[k]);
+      }
+    }
+  } else {
+    const int iters = (w.count + NT - 1) / NT;
+    // software pipeline: the next row's loads are in flight while this row computes
+    T an[B_CPT];
+    auto load_row = [&](int itr_, T* dst) {
+      const int64_t r = w.start + (int64_t)itr_ * NT + team;
+      const bool v = itr_ < iters && r < r1;
+      const T* Ar = A + (v ? r : w.start) * (int64_t)n;
+#pragma unroll
+      for (int k = 0; k < B_CPT; ++k) {
+        const int j = lt + k * TEAM;
+        dst[k] = (k < cpt && v && j < n) ? __ldcs(Ar + j) : T(0);
+      }
+    };
+    load_row(0, an);
+    for (int itr = 0; itr < iters; ++itr) {
+      const int64_t r = w.start + (int64_t)itr * NT + team;
+      const bool valid = r < r1;
+      T av[B_CPT];
+#pragma unroll
+      for (int k = 0; k < B_CPT; ++k) av[k] = an[k];
+      load_row(itr + 1, an);
+      {
+        T d = T(0);
 #pragma unroll
         for (int k = 0; k < B_CPT; ++k)
-          if (k < cpt) xbn[k] = fma(yb, av[k], xbn[k]);
+          if (k < cpt) d = fma(av[k], xv[k], d);
+#pragma unroll
+        for (int o = (TEAM < 32 ? TEAM : 32) / 2; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        if constexpr (TEAM > 32) {
+          constexpr int TW = TEAM / 32;
+          T* rt = reinterpret_cast<T*>(red) + (itr & 1) * BW + team * TW;
+          if (lane == 0) rt[warp % TW] = d;
+          team_barrier<TEAM>(team);
+          d = rt[0];
+#pragma unroll
+          for (int q = 1; q < TW; ++q) d += rt[q];
+        }
+        if (valid) {
+          fn.add(d);
+          const T yb = T(2) * d;
+#pragma unroll
+          for (int k = 0; k < B_CPT; ++k)
+            if (k < cpt) xbn[k] = fma(yb, av[k], xbn[k]);
+        }
       }
     }
   }

@@ -29,14 +29,7 @@ __device__ __forceinline__ Acc shfl_xor_acc2(Acc a, int o) {
   return b;
 }
 
-// Sinks receive contribution k (0..3, the element's local vertex) for global
-// vertex v.  sink_pair gives a sink the float-pair value of the pair kernels;
-// by default it is converted to double first.
-__device__ __forceinline__ float shfl_v(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-__device__ __forceinline__ double shfl_v(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
-__device__ __forceinline__ Acc shfl_v(Acc v, int src) {
-  return Acc{__shfl_sync(0xffffffffu, v.s, src), __shfl_sync(0xffffffffu, v.l, src)};
-}
+// Shift-down by d lanes of a value of the warp combine's types.
 __device__ __forceinline__ float shfl_down_v(float v, int d) {
   return __shfl_down_sync(0xffffffffu, v, d);
 }
@@ -47,6 +40,9 @@ __device__ __forceinline__ Acc shfl_down_v(Acc v, int d) {
   return Acc{__shfl_down_sync(0xffffffffu, v.s, d), __shfl_down_sync(0xffffffffu, v.l, d)};
 }
 
+// Sinks receive contribution k (0..3, the element's local vertex) for global
+// vertex v.  sink_pair gives a sink the float-pair value of the pair kernels;
+// by default it is converted to double first.
 template <typename T>
 struct AtomicSink {
   T* gu;
