@@ -716,10 +716,10 @@ _TRAFFIC = {
                        "10b3ebb054781b7d"),
     ("dense32", "f32"): (403951104, ["quadform_f32.cu", "kg_pair.cuh", "kg_device.cuh"],
                          "a2f7a0d457fa7b5a"),
-    ("tet", "f64"): (708191488, ["tet_pair.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
-                     "d2d68897e97ebdec"),
-    ("tet32", "f32"): (394469120, ["tet.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
-                       "d301a60c5512b91b"),
+    ("tet", "f64"): (708342528, ["tet_pair.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
+                     "c062cc9df2927b68"),
+    ("tet32", "f32"): (394994176, ["tet.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
+                       "dddf18082dcb690f"),
 }
 
 
