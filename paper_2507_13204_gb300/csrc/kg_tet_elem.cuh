@@ -6,7 +6,7 @@
 // The scatter-add goes through a sink: AtomicSink adds straight into gu in
 // global memory; HashSink first combines the contributions of a tile of
 // elements per vertex in a shared-memory open-addressing table (Sec. 5:
-// shared memory for temporaries), which hash_flush then adds into gu with one
+// temporaries kept in shared memory), which hash_flush then adds into gu with one
 // global atomic per distinct vertex; CollectSink keeps them in registers for
 // warp_combine, which merges equal vertices across the lanes of a warp.
 #pragma once
