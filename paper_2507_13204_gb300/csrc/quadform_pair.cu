@@ -239,6 +239,207 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
   }
 }
 
+// Warp-specialized fused value+gradient on the prepared A, for 2048 < n <= 10240.
+// All warps of qf_pair_kernel meet at the per-row barrier and then run the
+// row's latency-bound reduction together; here the work is split by role so
+// that one role's reduction overlaps the other's streaming FMAs:
+//   - warps 0..6 (dot): hold x as float pairs, column pairs jp = t + 224 k
+//     (k < KPD); each warp's partial of y_i goes to a two-row buffer and a
+//     y-ready mbarrier;
+//   - warps 7..14 (update): hold xbar, column pairs jp = t + 256 k (k < KP);
+//     for row i they sum the 7 partials in warp order, then accumulate
+//     xbar_j += 2 fbar y_i A_ij chunk by chunk and release each chunk;
+//   - warp 15 (lane 0): issues the TMA copies.
+// Rows stream in two chunks, pairs [0, H) and [H, n/2) with H = 128 KP, through a
+// ring of WS_SLOTS chunk slots: the row being updated, the row being reduced
+// and the next copy fit in shared memory.  From the ring depth (5 slots, 2
+// chunks a row): the dot warps reach row i + 2 only after the slot of row i's
+// first chunk was refilled, i.e. after the update warps read row i's partials,
+// so the two-row partial buffer and each y-ready barrier are never more than
+// one phase ahead.  All waits are bounded and report KG_ERR_TIMEOUT.
+constexpr int WS_DW = 7, WS_UW = 8;             // dot and update warps
+constexpr int WS_THREADS = (WS_DW + WS_UW + 1) * 32;
+constexpr int WS_SLOTS = 5;
+
+template <int KP>
+__global__ void __launch_bounds__(WS_THREADS, 1) qf_pair_ws_kernel(QpArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  constexpr int H = 128 * KP;                       // column pairs of a chunk slot
+  constexpr int TD = WS_DW * 32, TU = WS_UW * 32;   // 224 and 256 threads
+  constexpr int KPD = (KP * TU + TD - 1) / TD;      // dot pairs per thread
+  const int n = a.n, npairs = n >> 1;
+  float4* slots = reinterpret_cast<float4*>(smem);
+  uint64_t* full = reinterpret_cast<uint64_t*>(slots + WS_SLOTS * H);
+  uint64_t* empty = full + WS_SLOTS;
+  uint64_t* yready = empty + WS_SLOTS;                      // [2]
+  Acc* dpart = reinterpret_cast<Acc*>(yready + 2);         // [2][8]
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(dpart + 16);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t r0 = (int64_t)blockIdx.x * a.band;
+  const int64_t r1 = r0 + a.band < a.m ? r0 + a.band : a.m;
+  const int nrows = r1 > r0 ? (int)(r1 - r0) : 0;
+  const int nchunks = 2 * nrows;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < WS_SLOTS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], WS_UW);
+    }
+    mbar_init(&yready[0], WS_DW);
+    mbar_init(&yready[1], WS_DW);
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  if (warp < WS_DW) {
+    // ------------------------------------------------------------- dot role
+    const int t = threadIdx.x;
+    float xh[KPD][2], xl[KPD][2];
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < KPD; ++k) {
+      const int jp = t + TD * k;
+      double2 xv = make_double2(0.0, 0.0);
+      if (jp < npairs) xv = reinterpret_cast<const double2*>(a.x)[jp];
+      bad |= !pair_in_range(xv.x) || !pair_in_range(xv.y);
+      const Pair p0 = split_f64(xv.x), p1 = split_f64(xv.y);
+      xh[k][0] = p0.h;
+      xl[k][0] = p0.l;
+      xh[k][1] = p1.h;
+      xl[k][1] = p1.l;
+    }
+    if (bad) set_error(a.err, ERRBIT_RANGE);
+    for (int r = 0; r < nrows; ++r) {
+      if (*abort_flag) break;
+      const int s0 = (2 * r) % WS_SLOTS, s1 = (2 * r + 1) % WS_SLOTS;
+      bool ok = mbar_wait_bounded(&full[s0], (uint32_t)((2 * r) / WS_SLOTS) & 1u);
+      ok = ok && mbar_wait_bounded(&full[s1], (uint32_t)((2 * r + 1) / WS_SLOTS) & 1u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) set_error(a.err, ERRBIT_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      const float4* buf0 = slots + s0 * H;
+      const float4* buf1 = slots + s1 * H;
+      Acc yc[4] = {acc_zero(), acc_zero(), acc_zero(), acc_zero()};
+#pragma unroll
+      for (int k = 0; k < KPD; ++k) {
+        const int jp = t + TD * k;
+        if (jp < npairs) {
+          const float4 q = jp < H ? buf0[jp] : buf1[jp - H];
+          acc_fma(yc[2 * (k & 1)], q.x, q.y, xh[k][0], xl[k][0]);
+          acc_fma(yc[2 * (k & 1) + 1], q.z, q.w, xh[k][1], xl[k][1]);
+        }
+      }
+      Acc yv = acc_add(acc_add(yc[0], yc[1]), acc_add(yc[2], yc[3]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) yv = acc_add(yv, shfl_xor_acc(yv, o));
+      if (lane == 0) {
+        dpart[(r & 1) * 8 + warp] = yv;
+        mbar_arrive(&yready[r & 1]);
+      }
+      __syncwarp();
+    }
+  } else if (warp < WS_DW + WS_UW) {
+    // ---------------------------------------------------------- update role
+    const int t = threadIdx.x - TD;
+    const double fb = a.seed ? *a.seed : 1.0;
+    if (t == 0 && !pair_in_range(2.0 * fb)) set_error(a.err, ERRBIT_RANGE);
+    const Pair fb2 = split_f64(2.0 * fb);
+    Acc xb[KP][2];
+#pragma unroll
+    for (int k = 0; k < KP; ++k) xb[k][0] = xb[k][1] = acc_zero();
+    Acc facc = acc_zero();
+    for (int r = 0; r < nrows; ++r) {
+      if (*abort_flag) break;
+      bool ok = mbar_wait_bounded(&yready[r & 1], (uint32_t)(r >> 1) & 1u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) set_error(a.err, ERRBIT_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      Acc ya = dpart[(r & 1) * 8];
+#pragma unroll
+      for (int w = 1; w < WS_DW; ++w) ya = acc_add(ya, dpart[(r & 1) * 8 + w]);
+      const Pair y = acc_pair(ya);
+      if (t == 0) {
+        const Pair y2 = pair_mul(y, y);
+        facc = acc_add(facc, Acc{y2.h, y2.l});
+      }
+      const Pair yb = pair_mul(fb2, y);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int g = 2 * r + c, slot = g % WS_SLOTS;
+        // completed before the dot warps published y_i; the wait orders the copy's data
+        ok = ok && mbar_wait_bounded(&full[slot], (uint32_t)(g / WS_SLOTS) & 1u);
+        if (ok) {
+          const float4* buf = slots + slot * H;
+#pragma unroll
+          for (int kk = 0; kk < KP / 2; ++kk) {
+            const int k = c * (KP / 2) + kk;
+            if (t + TU * k < npairs) {
+              const float4 q = buf[t + TU * kk];
+              acc_fma(xb[k][0], q.x, q.y, yb.h, yb.l);
+              acc_fma(xb[k][1], q.z, q.w, yb.h, yb.l);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+      }
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) set_error(a.err, ERRBIT_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      if ((r & 15) == 15) {
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+          acc_renorm(xb[k][0]);
+          acc_renorm(xb[k][1]);
+        }
+      }
+    }
+    float4* out = a.partials + (int64_t)blockIdx.x * npairs;
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+      const int jp = t + TU * k;
+      if (jp < npairs) {
+        const Pair p0 = acc_pair(xb[k][0]), p1 = acc_pair(xb[k][1]);
+        out[jp] = make_float4(p0.h, p0.l, p1.h, p1.l);
+      }
+    }
+    if (t == 0) a.fpart[blockIdx.x] = acc_to_double(facc);
+  } else if (lane == 0) {
+    // ----------------------------------------------------- producer (TMA)
+    const uint32_t c0 = (uint32_t)H * 16u, c1 = (uint32_t)(npairs - H) * 16u;
+    const uint32_t row_bytes = (uint32_t)n * 8u;
+    int issued = 0;
+    for (int g = 0; g < nchunks; ++g) {
+      if (*abort_flag) break;
+      const int slot = g % WS_SLOTS;
+      if (g >= WS_SLOTS && !mbar_wait_bounded(&empty[slot], (uint32_t)(g / WS_SLOTS - 1) & 1u)) {
+        set_error(a.err, ERRBIT_TIMEOUT);
+        *abort_flag = 1;
+        break;
+      }
+      const int r = g >> 1, c = g & 1;
+      const double* row = a.A + (r0 + r) * (int64_t)n;
+      mbar_arrive_expect_tx(&full[slot], c ? c1 : c0);
+      tma_load_1d(slots + slot * H, row + (c ? 2 * H : 0), c ? c1 : c0, &full[slot]);
+      ++issued;
+      if (c == 0 && r + 2 < nrows) prefetch_l2_bulk(row + 2 * (int64_t)n, row_bytes);
+    }
+    // do not leave with a copy into this CTA's shared memory in flight
+    for (int g = issued - WS_SLOTS > 0 ? issued - WS_SLOTS : 0; g < issued; ++g)
+      mbar_wait_bounded(&full[g % WS_SLOTS], (uint32_t)(g / WS_SLOTS) & 1u);
+  }
+  __syncwarp();
+  __syncthreads();
+}
+
 // Fixed-order sum of the per-CTA float-pair partials: thread (cx, py) adds
 // partials py, py+16, ... of column pair cx; the 16 sums are then added in py
 // order and converted to double once per column.  Block 0 also writes f.
@@ -449,14 +650,47 @@ kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s) {
   return e == cudaSuccess ? KG_OK : cuda_fail(e, "qf pair forward kernel");
 }
 
+// Column pairs per role thread of qf_pair_ws_kernel (0: not used for this n).
+static int ws_kp(const kg_problem* p) {
+  if (!p->aprep || p->n <= 2048 || p->n > 10240) return 0;
+  return 4 * (int)((p->n / 2 + 1023) / 1024);
+}
+
+static size_t ws_smem(int kp) {
+  return (size_t)WS_SLOTS * 128 * kp * 16 + (2 * WS_SLOTS + 2) * 8 + 16 * sizeof(Acc) + 16;
+}
+
+template <int KP>
+static cudaError_t launch_ws(int grid, cudaStream_t s, const QpArgs& a) {
+  auto kern = qf_pair_ws_kernel<KP>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ws_smem(KP));
+  if (e != cudaSuccess) return e;
+  kern<<<grid, WS_THREADS, ws_smem(KP), s>>>(a);
+  return cudaGetLastError();
+}
+
+static cudaError_t dispatch_ws(int kp, int grid, cudaStream_t s, const QpArgs& a) {
+  switch (kp) {
+    case 8: return launch_ws<8>(grid, s, a);
+    case 12: return launch_ws<12>(grid, s, a);
+    case 16: return launch_ws<16>(grid, s, a);
+    case 20: return launch_ws<20>(grid, s, a);
+  }
+  return cudaErrorInvalidValue;
+}
+
 kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
                        int accumulate, cudaStream_t s) {
   if ((reinterpret_cast<uintptr_t>(x) & 15u) != 0 || (reinterpret_cast<uintptr_t>(gx) & 15u) != 0)
     return fail(KG_ERR_INVALID_ARG, "QUADFORM pair kernels need 16-byte aligned x and gx");
   QpArgs a = pair_args(p, x, seed);
-  prof_begin(s, p->aprep ? "qf_pair_kernel<fused, prepared A>" : "qf_pair_kernel<fused>");
-  cudaError_t e = dispatch_pair<true>(p->aprep != nullptr, pair_ppt(p->n), p->qf.grid,
-                                      pair_smem((int)p->n), s, a);
+  const int kp = ws_kp(p);
+  prof_begin(s, kp ? "qf_pair_ws_kernel<fused, prepared A>"
+                  : p->aprep ? "qf_pair_kernel<fused, prepared A>" : "qf_pair_kernel<fused>");
+  cudaError_t e = kp ? dispatch_ws(kp, p->qf.grid, s, a)
+                     : dispatch_pair<true>(p->aprep != nullptr, pair_ppt(p->n), p->qf.grid,
+                                           pair_smem((int)p->n), s, a);
   prof_end(s);
   count_launch();
   if (e != cudaSuccess) return cuda_fail(e, "qf pair fused kernel");

@@ -128,7 +128,10 @@ def test_pair_and_native_arithmetic_both_match(api, m, n):
 def test_prepared_and_on_the_fly_split_agree(api, m, n):
     # within the workspace budget kg_create keeps A split into float pairs and the kernels
     # stream that copy; a budget below 8 m n bytes makes them split A on every call.  The
-    # split is the same function either way, so both give bitwise identical results.
+    # split is the same function either way, so the forward (one kernel for both) gives
+    # bitwise identical results.  The gradient on the prepared copy runs the
+    # warp-specialized kernel for 2048 < n <= 10240, whose summation order differs from
+    # the on-the-fly kernel's: there the two agree to 1e-13 and each matches the oracle.
     A, x = W.quadform_inputs(n, m=m, seed=n + 2 * m)
     f_ref, g_ref = O.quadform_grad(A, x)
     At, xt = torch.tensor(A, device="cuda"), torch.tensor(x, device="cuda")
@@ -145,8 +148,13 @@ def test_prepared_and_on_the_fly_split_agree(api, m, n):
         assert rel_scalar(fe.item(), f_ref) <= TOL["f64"]
         assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
         out.append((f.clone(), g.clone(), fe.clone()))
-    for a, b in zip(*out):
-        assert torch.equal(a, b)
+    (fp, gp, ep), (ff, gf, ef) = out
+    assert torch.equal(ep, ef)
+    if 2048 < n <= 10240:
+        assert rel_scalar(fp.item(), ff.item()) <= 1e-13
+        assert rel_l2(gp.cpu().numpy(), gf.cpu().numpy()) <= 1e-13
+    else:
+        assert torch.equal(fp, ff) and torch.equal(gp, gf)
 
 
 def test_pair_is_default_for_f64_and_reproducible(api):
