@@ -19,6 +19,9 @@
 //     instructions per entry);
 //   - the private xbar partials (float pairs) of each CTA go to a workspace that
 //     a second kernel sums in a fixed order: bitwise reproducible.
+// For 2048 < n <= 10240 on the prepared A the fused pass runs qf_pair_ws_kernel
+// instead, with dot-product, update and copy roles in separate warps (described
+// at the kernel); the forward and all other shapes use qf_pair_kernel.
 // All waits are bounded (about one second) and report KG_ERR_TIMEOUT.
 #include <cuda_runtime.h>
 
