@@ -208,3 +208,24 @@ def test_pair_exact_cases(api):
     f, g = q.grad(torch.tensor(x, device="cuda"))
     _, g_ref = O.quadform_grad(A, x)
     assert rel_l2(g.cpu().numpy(), g_ref) <= 2e-14
+
+
+@pytest.mark.parametrize("m,n", [(1, 2050), (77, 4098), (200, 6146), (151, 8194), (500, 10240)])
+def test_warp_specialized_fused_kernel_shapes(api, m, n):
+    # 2048 < n <= 10240 on the prepared A runs the warp-specialized fused kernel: every
+    # chunk width (column pairs per update thread 8, 12, 16, 20), a single row, ragged row
+    # counts per CTA; a seed, and the same result on a second call
+    A, x = W.quadform_inputs(n, m=m, seed=m + n)
+    f_ref, g_ref = O.quadform_grad(A, x, fbar=0.5)
+    p = api.QuadForm(torch.tensor(A, device="cuda"))
+    assert p.config == ("fused", "recompute", "pair")
+    xt = torch.tensor(x, device="cuda")
+    seed = torch.tensor(0.5, dtype=torch.float64, device="cuda")
+    f, g = p.grad(xt, seed=seed)
+    f1, g1 = f.clone(), g.clone()
+    f, g = p.grad(xt, seed=seed)
+    p.sync()
+    assert rel_scalar(f1.item(), f_ref) <= TOL["f64"]
+    assert rel_l2(g1.cpu().numpy(), g_ref) <= TOL["f64"]
+    assert torch.equal(f, f1) and torch.equal(g, g1)
+    p.close()
