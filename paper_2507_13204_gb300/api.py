@@ -28,6 +28,32 @@ def _dev_tensor(t: torch.Tensor, dtype=None) -> torch.Tensor:
     return t
 
 
+def _arg(t, n: int, dtype, device, what: str, host: bool = False):
+    """A tensor the library reads or writes n elements of.  Checked here, so that a wrong
+    device, dtype, layout or length raises before any copy or kernel touches it (four
+    cheap queries on the fast path; the message is built only on failure)."""
+    if t is None:
+        return None
+    if (not isinstance(t, torch.Tensor) or t.dtype is not dtype or t.numel() != n
+            or not t.is_contiguous() or (t.is_cuda if host else t.device != device)):
+        _arg_error(t, n, dtype, device, what, host)
+    return t
+
+
+def _arg_error(t, n, dtype, device, what, host):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"kg: {what} must be a torch.Tensor")
+    if host and t.is_cuda:
+        raise ValueError(f"kg: {what} must be a host tensor")
+    if not host and t.device != device:
+        raise ValueError(f"kg: {what} must be a CUDA tensor on {device}")
+    if t.dtype != dtype:
+        raise ValueError(f"kg: {what} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"kg: {what} must be contiguous")
+    raise ValueError(f"kg: {what} must have {n} elements, has {t.numel()}")
+
+
 class Problem:
     kind = 0
 
@@ -61,42 +87,62 @@ class Problem:
     def nx(self) -> int:
         raise NotImplementedError
 
+    @property
+    def ndata(self) -> int:
+        """Length of gdata, the gradient w.r.t. the first data operand (0: not offered)."""
+        return 0
+
+    def _vec(self, t, what, host=False):
+        return _arg(t, self.nx, self.dtype, self.device, what, host)
+
+    def _one(self, t, what, host=False):
+        return _arg(t, 1, self.dtype, self.device, what, host)
+
     def _scalar(self):
         return torch.empty((), dtype=self.dtype, device=self.device)
 
     # -- calls
     def eval(self, x, f=None, stream=None):
-        f = self._scalar() if f is None else f
-        L.kg_eval(self.handle, _dev_tensor(x, self.dtype), f, stream)
+        f = self._scalar() if f is None else self._one(f, "f")
+        L.kg_eval(self.handle, self._vec(x, "x"), f, stream)
         return f
 
     def grad(self, x, gx=None, f=None, gdata=None, seed=None, accumulate=False, stream=None):
-        gx = torch.empty(self.nx, dtype=self.dtype, device=self.device) if gx is None else gx
-        f = self._scalar() if f is None else f
-        L.kg_grad(self.handle, _dev_tensor(x, self.dtype), f, gx, gdata, seed, int(accumulate), stream)
+        gx = torch.empty(self.nx, dtype=self.dtype, device=self.device) if gx is None else self._vec(gx, "gx")
+        f = self._scalar() if f is None else self._one(f, "f")
+        if gdata is not None:
+            if not self.ndata:
+                raise ValueError("kg: this kind offers no gradient w.r.t. its data (gdata)")
+            _arg(gdata, self.ndata, self.dtype, self.device, "gdata")
+        L.kg_grad(self.handle, self._vec(x, "x"), f, gx, gdata, self._one(seed, "seed"),
+                  int(accumulate), stream)
         return f, gx
 
     def hvp(self, x, v, hv=None, seed=None, accumulate=False, stream=None):
         """Hessian-vector product fbar * H(x) v (x may be None for the quadratic kinds)."""
-        hv = torch.empty(self.nx, dtype=self.dtype, device=self.device) if hv is None else hv
-        L.kg_hvp(self.handle, None if x is None else _dev_tensor(x, self.dtype),
-                 _dev_tensor(v, self.dtype), hv, seed, int(accumulate), stream)
+        hv = torch.empty(self.nx, dtype=self.dtype, device=self.device) if hv is None else self._vec(hv, "hv")
+        L.kg_hvp(self.handle, self._vec(x, "x"), self._vec(v, "v"), hv, self._one(seed, "seed"),
+                 int(accumulate), stream)
         return hv
 
     def eval_tape(self, x, f=None, stream=None):
         """Forward pass that records the problem's tape (TAPE mode)."""
-        f = self._scalar() if f is None else f
-        L.kg_eval_tape(self.handle, _dev_tensor(x, self.dtype), f, stream)
+        f = self._scalar() if f is None else self._one(f, "f")
+        L.kg_eval_tape(self.handle, self._vec(x, "x"), f, stream)
         return f
 
     def grad_from_tape(self, gx=None, seed=None, accumulate=False, stream=None):
         """Reverse pass from the tape of the last eval_tape."""
-        gx = torch.empty(self.nx, dtype=self.dtype, device=self.device) if gx is None else gx
-        L.kg_grad_from_tape(self.handle, gx, seed, int(accumulate), stream)
+        gx = torch.empty(self.nx, dtype=self.dtype, device=self.device) if gx is None else self._vec(gx, "gx")
+        L.kg_grad_from_tape(self.handle, gx, self._one(seed, "seed"), int(accumulate), stream)
         return gx
 
     def grad_host(self, x_host, gx_host, f_host=None, stream=None):
-        L.kg_grad_host(self.handle, x_host, f_host, gx_host, stream)
+        """kg_grad on host buffers (pinned for overlap): the library copies x in and
+        gx (and f) out."""
+        L.kg_grad_host(self.handle, self._vec(x_host, "x_host", host=True),
+                       self._one(f_host, "f_host", host=True), self._vec(gx_host, "gx_host", host=True),
+                       stream)
 
     def sync(self):
         L.kg_sync(self.handle)
@@ -125,6 +171,10 @@ class QuadForm(Problem):
     def nx(self):
         return self.n
 
+    @property
+    def ndata(self):
+        return self.m * self.n
+
 
 class SpQuadForm(Problem):
     """f(x) = ||A x||^2, A (m x n) sparse in compressed sparse rows on the device:
@@ -145,6 +195,10 @@ class SpQuadForm(Problem):
     @property
     def nx(self):
         return self.n
+
+    @property
+    def ndata(self):
+        return self.nnz
 
 
 class TetEnergy(Problem):
@@ -177,6 +231,10 @@ class Laplace1D(Problem):
     def nx(self):
         return self.n
 
+    @property
+    def ndata(self):
+        return self.n
+
 
 class Batch:
     """Many problems differentiated by one persistent launch (graph-replayed)."""
@@ -192,10 +250,29 @@ class Batch:
         """(arith, work items, persistent grid)."""
         return L.kg_batch_get_config(self.handle)
 
+    def _check(self, xs, fs, gxs):
+        # Lengths only: a batch call passes thousands of tensors, and checking each
+        # would cost more host time than the batch takes on the GPU.  Entry i must be
+        # laid out as for problems[i].grad (device, dtype, contiguous, nx elements;
+        # fs[i] one element or None); check_buffers() checks that once.
+        k = len(self.problems)
+        if len(xs) != k or len(fs) != k or len(gxs) != k:
+            raise ValueError(f"kg: the batch has {k} problems; xs, fs and gxs need one entry each")
+
+    def check_buffers(self, xs, fs, gxs):
+        """Full check of every entry of a set of batch buffers (call it once per set)."""
+        self._check(xs, fs, gxs)
+        for i, p in enumerate(self.problems):
+            p._vec(xs[i], f"xs[{i}]")
+            p._vec(gxs[i], f"gxs[{i}]")
+            p._one(fs[i], f"fs[{i}]")
+
     def grad(self, xs, fs, gxs, stream=None):
+        self._check(xs, fs, gxs)
         L.kg_grad_batched(self.handle, xs, fs, gxs, stream)
 
     def grad_loop(self, xs, fs, gxs, stream=None):
+        self._check(xs, fs, gxs)
         L.kg_grad_batched_loop(self.handle, xs, fs, gxs, stream)
 
     def sync(self):
