@@ -1036,15 +1036,50 @@ def run_reference(args, rank, world):
     O.build()
     if isinstance(wl, DenseWL):
         A, x = W.quadform_inputs(wl.n, seed=0)
-        rows = 1000
+        rows = min(1000, A.shape[0])
         A = A[:rows].copy()
         unit_bytes = wl.es * (rows * wl.n + 2 * wl.n)
         fn = lambda: O.quadform_grad(A, x)
         sample = f"value+grad of the first {rows} rows of the {wl.n}x{wl.n} problem per step"
         to_value = lambda s: unit_bytes / 1e9 / s
+    elif isinstance(wl, AutogradWL):
+        mesh, u = W.tet_inputs(wl.a)
+        wl.mesh, wl.u_host, wl.ne, wl.nv = mesh, u, mesh.ne, mesh.nv
+        wl.tape_bytes = 4 * wl.ne * wl.es
+        ne = min(mesh.ne, 500_000)
+        conn, G = mesh.conn[:ne], mesh.G[:ne]
+        state = {"u": u.copy()}
+
+        def fn():
+            _, g = O.tet_grad(conn, G, state["u"])
+            state["u"] = state["u"] - wl.ETA * g
+
+        sample = (f"one descent step (oracle gradient and update) on the first {ne} tets of the "
+                  f"{wl.a}^3 mesh per step, scaled to the full mesh")
+        to_value = lambda s: 1.0 / (s * wl.ne / ne)
+    elif isinstance(wl, BatchedWL):
+        sizes = W.batched_dense_sizes(wl.ndense)
+        boxes = W.batched_tet_boxes(wl.ntet)
+        wl.count = len(sizes) + len(boxes)
+        wl.grad_bytes = (sum(8 * (int(n) * int(n) + 2 * int(n)) for n in sizes)
+                         + sum(6 * a * b * c * (16 + 96) + 2 * (a + 1) * (b + 1) * (c + 1) * 8
+                               for a, b, c in boxes))
+        nd, nt = 16, 2  # the batch's 8 : 1 mix of dense and tet instances
+        dense = [W.batched_dense_instance(k, int(sizes[k])) for k in range(nd)]
+        tets = [W.batched_tet_instance(k, boxes[k]) for k in range(nt)]
+
+        def fn():
+            for A, x in dense:
+                O.quadform_grad(A, x)
+            for mesh, u in tets:
+                O.tet_grad(mesh.conn, mesh.G, u)
+
+        sample = f"{nd} dense and {nt} tet instances of the batch (its 8:1 mix) per step"
+        to_value = lambda s: (nd + nt) / s
     elif isinstance(wl, HvpWL):
         mesh, u = W.tet_inputs(wl.a)
-        ne = 500_000
+        wl.mesh, wl.u_host, wl.ne, wl.nv = mesh, u, mesh.ne, mesh.nv
+        ne = min(mesh.ne, 500_000)
         conn, G = mesh.conn[:ne], mesh.G[:ne]
         v = np.random.default_rng(43).uniform(-1.0, 1.0, mesh.nv)
         unit_bytes = ne * (16 + 12 * wl.es) + 3 * mesh.nv * wl.es
@@ -1053,7 +1088,8 @@ def run_reference(args, rank, world):
         to_value = lambda s: unit_bytes / 1e9 / s
     elif isinstance(wl, TetWL):
         mesh, u = W.tet_inputs(wl.a)
-        ne = 500_000
+        wl.mesh, wl.u_host, wl.ne, wl.nv = mesh, u, mesh.ne, mesh.nv
+        ne = min(mesh.ne, 500_000)
         conn, G = mesh.conn[:ne], mesh.G[:ne]
         unit_bytes = ne * (16 + 12 * wl.es) + 2 * mesh.nv * wl.es
         fn = lambda: O.tet_grad(conn, G, u)
@@ -1068,11 +1104,13 @@ def run_reference(args, rank, world):
         fn = lambda: O.spquadform_grad(A.rowptr, A.col, A.val, x)
         sample = f"one full value+grad of the {A.m}x{A.n} CSR problem per step"
         to_value = lambda s: wl.grad_bytes / 1e9 / s
-    else:
+    elif isinstance(wl, LaplaceWL):
         x, b = W.laplace1d_inputs(wl.n)
         fn = lambda: O.laplace1d_grad(x, b)
         sample = f"one value+grad at n={wl.n} per step"
         to_value = lambda s: 1.0 / s
+    else:
+        raise SystemExit(f"no oracle reference for workload {args.workload}")
     for _ in range(args.warmup):
         fn()
     K = args.steps if args.steps > 0 else 10

@@ -69,3 +69,20 @@ def test_reference_arm_prints_on_rank_zero_only():
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["cpu_baseline"]["kind"] == "oracle"
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+@pytest.mark.parametrize("workload,size", [
+    ("dense", 600), ("dense32", 600), ("dense64", 0), ("tet", 12), ("tet32", 12), ("tetcsr", 12),
+    ("hvp", 12), ("hvp32", 12), ("autograd", 12), ("autograd32", 12), ("sparse", 20000),
+    ("sparse32", 20000), ("batched", 16), ("laplace", 0), ("laplace_atomic", 0)])
+def test_reference_arm_covers_every_workload(workload, size):
+    # the oracle arm needs no GPU: every workload prints one line with its own config and unit
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1", LOCAL_RANK="0")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", workload,
+           "--steps", "1", "--warmup", "3"] + (["--size", str(size)] if size else [])
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    import json
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["config"]["workload"]
+    assert line["cpu_baseline"]["value"] == line["value"] and line["e2e"]["d2h_bytes_per_step"] == 0
