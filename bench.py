@@ -568,11 +568,9 @@ class BatchedWL(Workload):
         done = 0
         k = 0
         host = []
-        for i in range(64):
-            A, x = self.A[i]
+        for A, x in self.A[:64]:
             host.append(("d", A.cpu().numpy(), x.cpu().numpy()))
-        for j in range(8):
-            mesh, u, _, _ = self.tets[j]
+        for mesh, u, _, _ in self.tets[:8]:
             host.append(("t", mesh, u))
         t0 = time.perf_counter()
         while time.perf_counter() - t0 < budget_s and k < 4 * len(host):
@@ -584,7 +582,9 @@ class BatchedWL(Workload):
             done += 1
             k += 1
         dt = time.perf_counter() - t0
-        return done / dt, f"{done} instances (first 64 dense + first 8 tet instances, cycled; oracle, 1 thread)"
+        nd, nt = min(64, len(self.A)), min(8, len(self.tets))
+        return done / dt, (f"{done} instances (first {nd} dense + first {nt} tet instances, cycled; "
+                           f"oracle, 1 thread)")
 
 
 class AutogradWL(Workload):

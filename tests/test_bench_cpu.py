@@ -1,8 +1,11 @@
 """Host logic of bench.py: the recorded DRAM traffic is reported only at the default sizes and
-only while the dominant kernel's sources are unchanged since the ncu capture."""
+only while the dominant kernel's sources are unchanged since the ncu capture; every
+workload's CPU-baseline leg runs on the host data its set-up makes."""
 import os
 import shutil
 import sys
+
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
@@ -42,3 +45,36 @@ def test_traffic_is_null_once_a_kernel_source_changes_but_not_for_comments(tmp_p
         fh.write("\nstatic int edited_code = 1;\n")
     assert bench.recorded_traffic("dense", "f64", True) is None
     assert bench.recorded_traffic("dense32", "f32", True) == tb  # other sources untouched
+
+
+def _host_workload(name):
+    """A workload with only the host-side data its CPU-baseline leg reads (what its GPU
+    set-up would also have made), at a small size."""
+    import numpy as np
+    import torch
+    from paper_2507_13204_gb300 import workloads as W
+    wl = bench.make_workload(name, "auto", {"dense": 300, "batched": 16, "laplace": 500,
+                                            "sparse": 5000}.get(name, 6), 0)
+    if name == "dense":
+        wl.A_host, wl.x_host = W.quadform_inputs(wl.n, seed=0)
+        wl.m = wl.n
+    elif name == "sparse":
+        wl.A, wl.x_host = W.spquadform_inputs(wl.m)
+        wl.n, wl.nnz = wl.A.n, wl.A.nnz
+    elif name == "laplace":
+        wl.x_host, wl.b_host = W.laplace1d_inputs(wl.n)
+    elif name == "batched":
+        sizes, boxes = W.batched_dense_sizes(wl.ndense), W.batched_tet_boxes(wl.ntet)
+        wl.A = [tuple(torch.from_numpy(v) for v in W.batched_dense_instance(k, int(min(n, 64))))
+                for k, n in enumerate(sizes)]
+        wl.tets = [W.batched_tet_instance(k, b) + (None, None) for k, b in enumerate(boxes[:2])]
+    else:  # tet, hvp, autograd
+        wl.mesh, wl.u_host = W.tet_inputs(wl.a)
+        wl.ne, wl.nv = wl.mesh.ne, wl.mesh.nv
+    return wl
+
+
+@pytest.mark.parametrize("name", ["dense", "sparse", "laplace", "batched", "tet", "hvp", "autograd"])
+def test_cpu_baseline_legs_run_on_host_data(name):
+    value, sample = _host_workload(name).oracle_sample(budget_s=0.05)
+    assert value > 0 and "oracle" in sample
