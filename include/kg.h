@@ -186,7 +186,7 @@ void kg_options_default(kg_options *opt);
 kg_status kg_create(kg_problem **out, int kind, const int64_t *sizes, int nsizes,
                     const void *const *data, int ndata, const kg_options *opt, kg_stream s);
 
-/* Forward pass only: *f = f(x).  x: n (QUADFORM, LAPLACE1D) or N_v (TET). */
+/* Forward pass only: *f = f(x).  x: n (QUADFORM, SPQUADFORM, LAPLACE1D) or N_v (TET). */
 kg_status kg_eval(kg_problem *p, const void *x, void *f, kg_stream s);
 
 /* Value and gradient (the paper's gradient function: forward pass, seed,
