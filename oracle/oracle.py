@@ -2,7 +2,8 @@
 
 TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
 CPU-baseline leg load this module; the product path never does.  It shares no
-code with the CUDA path.
+code with the CUDA path.  The *_omp functions (kg_oracle_omp.c) are the timed
+CPU baseline on all host cores; parity is checked against the serial ones.
 
 All functions take and return float64 numpy arrays.  FP32 workloads are
 checked by calling these on the FP32-rounded inputs (the oracle itself always
@@ -38,6 +39,68 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True, capture_output=True)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+_SRC_OMP = os.path.join(_HERE, "kg_oracle_omp.c")
+_LIB_OMP = os.path.join(_HERE, "libkg_oracle_omp.so")
+_lib_omp = None
+
+
+def build_omp(force: bool = False) -> str:
+    """Compile kg_oracle_omp.c (the OpenMP CPU baseline) into libkg_oracle_omp.so."""
+    if (not force and os.path.exists(_LIB_OMP)
+            and os.path.getmtime(_LIB_OMP) >= os.path.getmtime(_SRC_OMP)):
+        return _LIB_OMP
+    tmp = _LIB_OMP + f".tmp{os.getpid()}"
+    cmd = ["gcc", *CFLAGS, "-fopenmp", "-o", tmp, _SRC_OMP, "-lm"]
+    subprocess.run(cmd, check=True, capture_output=True)
+    os.replace(tmp, _LIB_OMP)
+    return _LIB_OMP
+
+
+def _load_omp():
+    global _lib_omp
+    with _lock:
+        if _lib_omp is None:
+            lib = ctypes.CDLL(build_omp())
+            i64, dp, d = ctypes.c_int64, ctypes.c_void_p, ctypes.c_double
+            lib.kgo_omp_threads.argtypes = []
+            lib.kgo_omp_threads.restype = ctypes.c_int
+            lib.kgo_quadform_grad_omp.argtypes = [i64, i64, dp, dp, d, dp, dp, dp]
+            lib.kgo_quadform_grad_omp.restype = ctypes.c_int
+            lib.kgo_tet_grad_omp.argtypes = [i64, i64, dp, dp, dp, d, dp, dp, dp]
+            lib.kgo_tet_grad_omp.restype = ctypes.c_int
+            _lib_omp = lib
+    return _lib_omp
+
+
+def omp_threads() -> int:
+    """Threads the OpenMP CPU baseline uses (OMP_NUM_THREADS, else all cores)."""
+    return int(_load_omp().kgo_omp_threads())
+
+
+def quadform_grad_omp(A, x, fbar=1.0):
+    """CPU baseline on all cores: (f, gx, threads used).  Not a parity reference."""
+    A, x = _f64(A), _f64(x)
+    m, n = A.shape
+    f = np.zeros(1)
+    gx = np.empty(n)
+    t = ctypes.c_int(0)
+    _check(_load_omp().kgo_quadform_grad_omp(m, n, _p(A), _p(x), float(fbar), _p(f), _p(gx),
+                                             ctypes.addressof(t)), "quadform_grad_omp")
+    return float(f[0]), gx, t.value
+
+
+def tet_grad_omp(conn, G, u, fbar=1.0):
+    """CPU baseline on all cores: (f, gu, threads used).  Not a parity reference."""
+    conn, G, u = _i32(conn), _f64(G), _f64(u)
+    f = np.zeros(1)
+    gu = np.empty(u.shape[0])
+    t = ctypes.c_int(0)
+    _check(_load_omp().kgo_tet_grad_omp(conn.shape[0], u.shape[0], _p(conn), _p(G), _p(u),
+                                        float(fbar), _p(f), _p(gu), ctypes.addressof(t)),
+           "tet_grad_omp")
+    return float(f[0]), gu, t.value
 
 
 def _load():
