@@ -493,7 +493,9 @@ static kg_status qf_grad_t(kg_problem* p, const void* x, void* f, void* gx, void
 // Native FP64 fused value-and-gradient with every workspace taken from
 // `scratch` (partials: grid * n doubles, then grid f partials).  The fused
 // kernel writes all of them before the reduce kernel reads them, so the
-// scratch needs no clearing.  KG_ERR_INVALID_ARG if it is too small.
+// scratch needs no clearing.  The grid is capped at scratch_doubles / (n + 1)
+// CTAs (more rows per CTA instead), so any m fits once that cap is >= 1;
+// KG_ERR_INVALID_ARG otherwise.
 kg_status qf_native_fused_on_scratch(const double* A, int64_t m, int64_t n, const double* x,
                                      double* f, double* gx, double* scratch,
                                      size_t scratch_doubles, cudaStream_t s) {
@@ -503,7 +505,12 @@ kg_status qf_native_fused_on_scratch(const double* A, int64_t m, int64_t n, cons
   const int nteams = v.block / v.team;
   const int resident = v.block >= 512 ? 1 : 2;
   const int64_t target = (int64_t)num_sms() * resident;
-  const int64_t rows = std::max<int64_t>(nteams, (m + target - 1) / target);
+  const int64_t max_grid = (int64_t)(scratch_doubles / ((size_t)n + 1));
+  if (max_grid < 1)
+    return fail(KG_ERR_INVALID_ARG, "scratch of " + std::to_string(scratch_doubles) +
+                                        " doubles is too small for n = " + std::to_string(n));
+  const int64_t rows = std::max<int64_t>({(int64_t)nteams, (m + target - 1) / target,
+                                          (m + max_grid - 1) / max_grid});
   const int grid = (int)((m + rows - 1) / rows);
   const size_t need = (size_t)grid * (size_t)n + (size_t)grid;
   if (need > scratch_doubles)

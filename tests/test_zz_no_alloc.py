@@ -1,20 +1,24 @@
 """The allocation-free entry point kg_quadform_grad_noalloc, called through the
-C ABI, gives the same value and gradient as the problem-handle path (kg_grad)
-on two calls in a row.  It exists for callers that cannot allocate device
-memory: it takes its scratch from an array compiled into the library.
+C ABI, on two calls in a row: its value and gradient match the FP64 oracle and
+the problem-handle entry point kg_grad.  It exists for callers that cannot
+allocate device memory (code under a memory manager that owns the device heap,
+a loop that must never enter the allocator): it takes its scratch from an
+array compiled into the library.
 
 Kept in a file that is collected last, and self-contained, so that it passes
 alone in a fresh process as well as after the other tests."""
 import ctypes
 
-import numpy as np
 import pytest
 import torch
 
+from oracle import oracle as O
 from paper_2507_13204_gb300 import workloads as W
 from tests.helpers import TOL, rel_l2, rel_scalar
 
 pytestmark = pytest.mark.gpu
+
+N_MAX = 12288  # the entry point's documented limit on n
 
 
 @pytest.fixture(scope="module")
@@ -37,17 +41,23 @@ def _noalloc(L, A, x):
     return f, gx
 
 
-def test_noalloc_matches_kg_grad_on_two_calls_in_a_row(mods):
+@pytest.mark.parametrize("cases", [
+    [(4000, 10000, 0), (777, 3001, 1)],      # the second call reuses the scratch
+    [(3000, N_MAX, 2), (5, 1, 3)],           # the largest n, then a 5 x 1 problem
+])
+def test_noalloc_matches_oracle_and_kg_grad_on_two_calls_in_a_row(mods, cases):
     L, api = mods
-    cases = [(4000, 10000, 0), (777, 3001, 1)]  # the second call reuses the scratch
     results = []
     for m, n, seed in cases:
         A, x = W.quadform_inputs(n, m=m, seed=seed)
         At = torch.tensor(A, device="cuda")
         xt = torch.tensor(x, device="cuda")
-        results.append((At, xt, _noalloc(L, At, xt)))
+        results.append((A, x, At, xt, _noalloc(L, At, xt)))
     torch.cuda.synchronize()
-    for At, xt, (f, gx) in results:
+    for A, x, At, xt, (f, gx) in results:
+        f_or, g_or = O.quadform_grad(A, x)
+        assert rel_scalar(f.item(), f_or) <= TOL["f64"]
+        assert rel_l2(gx.cpu().numpy(), g_or) <= TOL["f64"]
         p = api.QuadForm(At)
         f_ref, g_ref = p.grad(xt)
         p.sync()
@@ -56,11 +66,12 @@ def test_noalloc_matches_kg_grad_on_two_calls_in_a_row(mods):
         p.close()
 
 
-def test_noalloc_rejects_sizes_beyond_its_scratch(mods):
+def test_noalloc_rejects_n_beyond_its_limit(mods):
     L, _ = mods
-    A = torch.zeros((4, 20000), dtype=torch.float64, device="cuda")
-    x = torch.zeros(20000, dtype=torch.float64, device="cuda")
+    n = N_MAX + 1
+    A = torch.zeros((4, n), dtype=torch.float64, device="cuda")
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
     with pytest.raises(L.KGError) as ei:
         _noalloc(L, A, x)
     assert ei.value.status == L.KG_ERR_INVALID_ARG
-    assert "12288" in str(ei.value)
+    assert str(N_MAX) in str(ei.value)
