@@ -121,3 +121,93 @@ def test_batch_rejects_bad_inputs(api):
     with pytest.raises(L.KGError) as ei:
         api.Batch([a, b])
     assert ei.value.status == L.KG_ERR_INVALID_ARG
+
+
+def _bucket(v):
+    return int(v).bit_length() - 1  # floor(log2 v), the library's size bucket
+
+
+def _items(dense_ns, tet_nes, rows, elems):
+    """Work items of a batch whose tiles are rows[bucket] rows (dense) and
+    elems[bucket] elements (tet), one item per tile."""
+    return (sum(-(-n // rows[_bucket(n)]) for n in dense_ns)
+            + sum(-(-ne // elems[_bucket(ne)]) for ne in tet_nes))
+
+
+def test_full_4096_dense_512_tet_batch_sampled_against_oracle(api, tmp_path, monkeypatch):
+    """The benchmarked batch (4096 dense instances, n log-uniform in [32, 2048],
+    A drawn on the device, plus 512 tet meshes of 1e3..1e5 elements), one
+    kg_grad_batched launch; sampled instances against the oracle: one dense
+    instance per size bucket (first and last of each), the smallest and the
+    largest n, the 8 largest and the smallest tet meshes, and the last instance.
+    Then the tuning cache: a second batch reads the tiles back per bucket."""
+    import json
+    monkeypatch.setenv("KG_TUNE_CACHE", str(tmp_path / "tune.json"))
+    dev = torch.device("cuda", 0)
+    sizes = [int(n) for n in W.batched_dense_sizes(4096)]
+    boxes = W.batched_tet_boxes(512)
+    probs, dense_dev, tets, nx = [], [], [], []
+    for k, n in enumerate(sizes):
+        A, x = W.batched_dense_device(k, n, dev)
+        dense_dev.append((A, x))
+        probs.append(api.QuadForm(A))
+        nx.append(n)
+    for k, box in enumerate(boxes):
+        mesh, u = W.batched_tet_instance(k, box)
+        conn, G = torch.tensor(mesh.conn, device=dev), torch.tensor(mesh.G, device=dev)
+        tets.append((mesh, u, conn, G))
+        probs.append(api.TetEnergy(conn, G, mesh.nv))
+        nx.append(mesh.nv)
+    xs = [x for _, x in dense_dev] + [torch.tensor(t[1], device=dev) for t in tets]
+    fs = [torch.empty((), dtype=torch.float64, device=dev) for _ in nx]
+    gxs = [torch.full((v,), 5.0, dtype=torch.float64, device=dev) for v in nx]
+    batch = api.Batch(probs)
+    arith, nitems, _ = batch.config
+    batch.grad(xs, fs, gxs)
+    batch.sync()
+
+    # the sample
+    by_bucket = {}
+    for k, n in enumerate(sizes):
+        by_bucket.setdefault(_bucket(n), []).append(k)
+    assert sorted(by_bucket) == list(range(5, 12))
+    dense_ids = {ks[0] for ks in by_bucket.values()} | {ks[-1] for ks in by_bucket.values()}
+    dense_ids |= {int(np.argmin(sizes)), int(np.argmax(sizes))}
+    nes = [t[0].ne for t in tets]
+    order = np.argsort(nes, kind="stable")
+    tet_ids = {int(j) for j in order[-8:]} | {int(order[0]), len(tets) - 1}
+    assert max(nes) > 90_000
+    for k in sorted(dense_ids):
+        A, x = dense_dev[k]
+        f_ref, g_ref = O.quadform_grad(A.cpu().numpy(), x.cpu().numpy())
+        assert rel_scalar(fs[k].item(), f_ref) <= TOL["f64"], (k, sizes[k])
+        assert rel_l2(gxs[k].cpu().numpy(), g_ref) <= TOL["f64"], (k, sizes[k])
+    for j in sorted(tet_ids):
+        mesh, u, _, _ = tets[j]
+        f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
+        i = len(sizes) + j
+        assert rel_scalar(fs[i].item(), f_ref) <= TOL["f64"], (j, mesh.ne)
+        assert rel_l2(gxs[i].cpu().numpy(), g_ref) <= TOL["f64"], (j, mesh.ne)
+
+    # the tuning cache holds one entry per (kind, bucket), and the work table follows it
+    cache = json.loads((tmp_path / "tune.json").read_text())
+    key = lambda kind, b: next(k for k in cache if k.endswith(f"|{arith}|{kind}|{b}"))
+    dense_b = sorted({_bucket(n) for n in sizes})
+    tet_b = sorted({_bucket(ne) for ne in nes})
+    rows = {b: cache[key("dense", b)] for b in dense_b}
+    elems = {b: cache[key("tet", b)] for b in tet_b}
+    assert nitems == _items(sizes, nes, rows, elems)
+    # a second batch over the same problems reads the tiles back from the cache
+    for r, e in ((4, 1024), (128, 16384)):
+        for b in dense_b:
+            cache[key("dense", b)] = r
+        for b in tet_b:
+            cache[key("tet", b)] = e
+        (tmp_path / "tune.json").write_text(json.dumps(cache, indent=2))  # one entry a line
+        second = api.Batch(probs)
+        assert second.config[1] == _items(sizes, nes, {b: r for b in dense_b},
+                                          {b: e for b in tet_b})
+        second.close()
+    batch.close()
+    for p in probs:
+        p.close()
