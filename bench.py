@@ -12,8 +12,9 @@ Multi-GPU (torchrun, one process per GPU): every rank runs an independent
 replica of the workload (the problems are independent; there is no data-path
 collective), timed between barriers; value = units of all ranks / max time.
 
---impl reference times the CPU oracle (plain C, one thread) on a bounded
-sample of the same workload, on rank 0 only.
+--impl reference times the CPU oracle on the same workload, on rank 0 only:
+the OpenMP build on all host cores for the dense and tet workloads (the full
+problem per step), the serial oracle on a bounded sample for the others.
 """
 from __future__ import annotations
 
@@ -65,9 +66,28 @@ class ClockSampler:
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index: int):
+        # nvidia-smi numbers GPUs physically; a single visible device is named by
+        # CUDA_VISIBLE_DEVICES when that is set
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+        parts = [v for v in vis.split(",") if v.strip()]
+        if parts and index < len(parts) and parts[index].strip().isdigit():
+            index = int(parts[index])
         self.index = index
         self.proc = None
         self.path = None
+
+    def wait_first_row(self, timeout_s: float = 5.0) -> bool:
+        """Blocks until nvidia-smi has written its first sample (or timeout)."""
+        t0 = time.perf_counter()
+        while self.proc is not None and time.perf_counter() - t0 < timeout_s:
+            self.fh.flush()
+            try:
+                if os.path.getsize(self.path) > 0:
+                    return True
+            except OSError:
+                return False
+            time.sleep(0.02)
+        return False
 
     def start(self):
         try:
@@ -97,17 +117,68 @@ class ClockSampler:
                 if len(parts) < 9:
                     continue
                 try:
-                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                    power = float(parts[3]) if parts[3].replace(".", "", 1).isdigit() else None
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9], power))
                 except ValueError:
                     continue
         os.unlink(self.path)
         if not rows:
             return None
+        # the first sample may predate the load; the median is over the rest
+        load = rows[1:] if len(rows) > 1 else rows
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for _, _, flags in rows for i, f in enumerate(flags)
+        reasons = sorted({names[i] for _, _, flags, _ in load for i, f in enumerate(flags)
                           if f.lower() == "active"})
-        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
-                "reasons": reasons, "samples": len(rows)}
+        powers = [r[3] for r in load if r[3] is not None]
+        return {"sm_mhz": statistics.median(r[0] for r in load), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows), "samples_under_load": len(load),
+                "power_w_max": max(powers) if powers else None}
+
+
+def fp64_peak(peaks, box):
+    """FP64 FMA peak for the ALU roofline: this run's kg_measure_box figure when
+    it is there, else the nominal issue rate."""
+    if box and box.get("fp64_fma_tflops", 0) > 0:
+        return box["fp64_fma_tflops"], "measured in this run (kg_measure_box: FP64 FMA chains)"
+    return peaks["fp64_tflops"], "nominal FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2070 MHz"
+
+
+def cpu_baseline_runs(omp_fn, serial_fn, bytes_omp, what, budget_s, serial_bytes=None,
+                      serial_what=None):
+    """The CPU baseline: the OpenMP build of the oracle on all host cores (about
+    60% of the budget), then the serial oracle (the rest).  Returns the
+    cpu_baseline record: GB/s of algorithmic bytes, threads actually used, and
+    the single-threaded figure beside it.  Without an OpenMP build, the serial
+    oracle alone (cores 1)."""
+    serial_bytes = bytes_omp if serial_bytes is None else serial_bytes
+    serial_what = what if serial_what is None else serial_what
+
+    def run(fn, nbytes, budget, cap):
+        t0 = time.perf_counter()
+        reps, out = 0, None
+        while True:
+            out = fn()
+            reps += 1
+            if time.perf_counter() - t0 >= budget or reps >= cap:
+                break
+        return reps * nbytes / 1e9 / (time.perf_counter() - t0), reps, out
+
+    single = None
+    try:
+        v, reps, out = run(omp_fn, bytes_omp, 0.6 * budget_s, 400)
+        cores = int(out[-1])
+        rec = {"value": round(v, 4), "cores": cores,
+               "sample": f"{reps} x {what} (oracle, OpenMP build, {cores} threads on the host cores)"}
+        sb = 0.4 * budget_s
+    except Exception as e:  # noqa: BLE001  (no OpenMP build on this host)
+        rec, sb = None, budget_s
+        single_note = f"OpenMP build unavailable: {e}"
+    v1, reps1, _ = run(serial_fn, serial_bytes, sb, 20)
+    single = {"value": round(v1, 4), "cores": 1,
+              "sample": f"{reps1} x {serial_what} (oracle, 1 thread)"}
+    if rec is None:
+        return {**single, "kind": "oracle", "note": single_note}
+    return {**rec, "kind": "oracle", "single_thread": single}
 
 
 # ------------------------------------------------------------------ workloads
@@ -192,17 +263,44 @@ class DenseWL(Workload):
 
     def oracle_sample(self, budget_s=10.0):
         from oracle import oracle as O
-        rows = self.m
-        t0 = time.perf_counter()
-        reps, done = 0, 0
-        while True:
-            O.quadform_grad(self.A_host[:rows], self.x_host)
-            reps += 1
-            done += self.es * (rows * self.n + 2 * self.n)
-            if time.perf_counter() - t0 >= budget_s or reps >= 20:
-                break
-        dt = time.perf_counter() - t0
-        return done / 1e9 / dt, f"{reps} x full {self.m}x{self.n} value+grad (oracle, 1 thread)"
+        A, x = self.A_host, self.x_host
+        return cpu_baseline_runs(
+            lambda: O.quadform_grad_omp(A, x), lambda: O.quadform_grad(A, x),
+            self.es * (self.m * self.n + 2 * self.n), f"full {self.m}x{self.n} value+grad",
+            budget_s)
+
+    def native_record(self, timed, peaks, box):
+        """The same value-and-gradient in native FP64 arithmetic (IEEE FP64
+        instructions throughout) on the same A: its step, forward, ratio, main
+        kernel and FP64-ALU fraction."""
+        import torch
+        from paper_2507_13204_gb300 import _lib as L, api
+        pn = api.QuadForm(self.At, strategy=self.strategy, arith="native")
+        gx = torch.empty_like(self.gx)
+        f, fe = torch.empty_like(self.f), torch.empty_like(self.fe)
+        grad = lambda: pn.grad(self.xt, gx=gx, f=f)
+        ev = lambda: pn.eval(self.xt, f=fe)
+        for _ in range(3):
+            grad()
+            ev()
+        t = timed(grad, 2)
+        k = max(10, min(2000, int(500.0 / max(t, 1e-3))))
+        L.kg_profile_enable(True)
+        ms = timed(grad, k)
+        kms, kn, kname = L.kg_profile_read()
+        L.kg_profile_enable(False)
+        ms_e = timed(ev, k)
+        pn.sync()
+        pn.close()
+        kus = kms / max(kn, 1) * 1e3
+        tf = 4.0 * self.m * self.n / 1e12 / (kus * 1e-6)
+        peak, src = fp64_peak(peaks, box)
+        return {"arith": "native", "ms_per_step": round(ms, 5), "ms_eval": round(ms_e, 5),
+                "grad_over_eval_ratio": round(ms / ms_e, 4), "kernel": kname,
+                "kernel_us": round(kus, 2), "fp64_tflops": round(tf, 4), "fp64_peak": round(peak, 4),
+                "fp64_frac": round(tf / peak, 4), "fp64_peak_source": src,
+                "hbm_gbs": round(self.grad_bytes / 1e9 / (ms * 1e-3), 1),
+                "flops_per_launch": 4 * self.m * self.n, "steps": k}
 
 
 class SparseWL(Workload):
@@ -343,18 +441,15 @@ class TetWL(Workload):
 
     def oracle_sample(self, budget_s=10.0):
         from oracle import oracle as O
-        ne = min(self.ne, 1_000_000)
-        conn, G = self.mesh.conn[:ne], self.mesh.G[:ne]
-        t0 = time.perf_counter()
-        reps = 0
-        while True:
-            O.tet_grad(conn, G, self.u_host)
-            reps += 1
-            if time.perf_counter() - t0 >= budget_s or reps >= 20:
-                break
-        dt = time.perf_counter() - t0
-        b = reps * (ne * (16 + 12 * self.es) + 2 * self.nv * self.es)
-        return b / 1e9 / dt, f"{reps} x value+grad of the first {ne} tets (oracle, 1 thread)"
+        conn, G, u = self.mesh.conn, self.mesh.G, self.u_host
+        ne1 = min(self.ne, 1_000_000)
+        c1, G1 = conn[:ne1], G[:ne1]
+        return cpu_baseline_runs(
+            lambda: O.tet_grad_omp(conn, G, u), lambda: O.tet_grad(c1, G1, u),
+            self.ne * (16 + 12 * self.es) + 2 * self.nv * self.es,
+            f"full {self.ne}-tet value+grad", budget_s,
+            serial_bytes=ne1 * (16 + 12 * self.es) + 2 * self.nv * self.es,
+            serial_what=f"value+grad of the first {ne1} tets")
 
 
 class HvpWL(TetWL):
@@ -841,6 +936,10 @@ def main():
         wl.step()
         wl.eval_step()
     torch.cuda.synchronize()
+    try:  # FP64 / FP32 FMA and red rates of this GPU (a few ms)
+        box = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in L.kg_measure_box().items()}
+    except Exception as e:  # noqa: BLE001
+        box = {"error": str(e)}
     wl.step()
     launches_per_step = L.kg_last_launch_count()
     wl.eval_step()
@@ -849,13 +948,33 @@ def main():
     t_probe = timed(wl.step, 3)
     K = args.steps if args.steps > 0 else max(10, min(20000, int(3000.0 / max(t_probe, 1e-3))))
 
+    def busy(fn, seconds):
+        """Untimed steps for `seconds` of wall time, synchronising every few
+        steps so that the host never runs far ahead of the GPU."""
+        chunk = max(1, int(20.0 / max(t_probe, 1e-3)))  # about 20 ms of steps
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < seconds:
+            for _ in range(chunk):
+                fn()
+            torch.cuda.synchronize()
+
+    # Clock record: nvidia-smi samples every 200 ms from before a second of
+    # untimed steps, through the timed steps, to half a second of untimed steps
+    # after them, so that it holds samples of this workload under load however
+    # short the timed region is.
     clocks = ClockSampler(local)
     clocks.start()
+    clocks.wait_first_row()
+    busy(wl.step, 1.0)
     L.kg_profile_enable(True)
     ms_grad = timed(wl.step, K)
     kern_ms, kern_n, kern_name = L.kg_profile_read()
     L.kg_profile_enable(False)
+    busy(wl.step, 0.5)
     clk = clocks.stop()
+    if clk is not None:
+        clk["window"] = ("nvidia-smi every 200 ms over 1 s of untimed steps, the timed steps "
+                         "and 0.5 s of untimed steps of the same workload")
     t_probe_e = timed(wl.eval_step, 1)
     Ke = max(3, min(K, int(3000.0 / max(t_probe_e, 1e-3))))
     ms_eval = timed(wl.eval_step, Ke)
@@ -873,6 +992,10 @@ def main():
     barrier()
     ms_e2e = (time.perf_counter() - t0) * 1e3 / K2
     (ms_e2e,) = sync_max([ms_e2e], dist, dev)
+
+    native = None
+    if isinstance(wl, DenseWL) and wl.dtype == "f64" and wl.p.config[2] == "pair":
+        native = wl.native_record(timed, peaks, box)
 
     if rank != 0:
         if dist:
@@ -904,12 +1027,13 @@ def main():
     native64 = wl.dtype_name == "f64" and arith == "native"
     if dflops and native64 and per_launch_ms > 0:
         ach_tf = dflops / 1e12 / (per_launch_ms * 1e-3)
-        frac_alu = ach_tf / peaks["fp64_tflops"]
+        fpk, fsrc = fp64_peak(peaks, box)
+        frac_alu = ach_tf / fpk
         if frac_alu > roof["frac"]:
-            roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(peaks["fp64_tflops"], 4),
+            roof = {"bound": "alu", "achieved": round(ach_tf, 4), "peak": round(fpk, 4),
                     "unit": "TFLOP/s", "frac": round(frac_alu, 4), "traffic": None,
                     "kernel": kern_name, "kernel_us": round(per_launch_ms * 1e3, 2),
-                    "peak_source": "FP64 FMA issue rate: 152 SMs x 2 FMA/clk x 2070 MHz",
+                    "peak_source": fsrc,
                     "hbm_gbs": round(ach_gbs, 1), "hbm_frac": round(ach_gbs / peaks["hbm_gbs"], 4)}
 
     out = {
@@ -944,11 +1068,20 @@ def main():
                         "instances": wl.count}} if isinstance(wl, BatchedWL) else {}),
         "launches_per_step": {"grad": launches_per_step, "eval": launches_eval},
         "clocks": clk,
+        **({"native_f64": native} if native else {}),
+        "box": box,
     }
     if world == 1 and not args.no_cpu_baseline:
-        v, sample = wl.oracle_sample()
-        out["cpu_baseline"] = {"value": round(v, 4), "unit": wl.unit, "cores": 1, "kind": "oracle",
-                               "sample": sample}
+        res = wl.oracle_sample()
+        if isinstance(res, dict):
+            out["cpu_baseline"] = {"value": res["value"], "unit": wl.unit, "cores": res["cores"],
+                                   "kind": "oracle", "sample": res["sample"],
+                                   **{k: v for k, v in res.items()
+                                      if k not in ("value", "cores", "kind", "sample")}}
+        else:
+            v, sample = res
+            out["cpu_baseline"] = {"value": round(v, 4), "unit": wl.unit, "cores": 1, "kind": "oracle",
+                                   "sample": sample}
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -1034,13 +1167,23 @@ def run_reference(args, rank, world):
     from paper_2507_13204_gb300 import workloads as W
     from oracle import oracle as O
     O.build()
+    cores = 1
     if isinstance(wl, DenseWL):
-        A, x = W.quadform_inputs(wl.n, seed=0)
-        rows = min(1000, A.shape[0])
-        A = A[:rows].copy()
-        unit_bytes = wl.es * (rows * wl.n + 2 * wl.n)
-        fn = lambda: O.quadform_grad(A, x)
-        sample = f"value+grad of the first {rows} rows of the {wl.n}x{wl.n} problem per step"
+        A, x = W.quadform_inputs(wl.n, m=wl.m, seed=0)
+        if wl.dtype == "f32":
+            A, x = A.astype("float32").astype("float64"), x.astype("float32").astype("float64")
+        unit_bytes = wl.es * (wl.m * wl.n + 2 * wl.n)
+        try:
+            cores = O.omp_threads()
+            fn = lambda: O.quadform_grad_omp(A, x)
+            sample = (f"full value+grad of the {wl.m}x{wl.n} problem per step (oracle, OpenMP "
+                      f"build, {cores} threads)")
+        except Exception:  # noqa: BLE001  (no OpenMP build: serial oracle on 1000 rows)
+            rows = min(1000, A.shape[0])
+            A = A[:rows].copy()
+            unit_bytes = wl.es * (rows * wl.n + 2 * wl.n)
+            fn = lambda: O.quadform_grad(A, x)
+            sample = f"value+grad of the first {rows} rows of the {wl.m}x{wl.n} problem per step"
         to_value = lambda s: unit_bytes / 1e9 / s
     elif isinstance(wl, AutogradWL):
         mesh, u = W.tet_inputs(wl.a)
@@ -1089,11 +1232,22 @@ def run_reference(args, rank, world):
     elif isinstance(wl, TetWL):
         mesh, u = W.tet_inputs(wl.a)
         wl.mesh, wl.u_host, wl.ne, wl.nv = mesh, u, mesh.ne, mesh.nv
-        ne = min(mesh.ne, 500_000)
-        conn, G = mesh.conn[:ne], mesh.G[:ne]
-        unit_bytes = ne * (16 + 12 * wl.es) + 2 * mesh.nv * wl.es
-        fn = lambda: O.tet_grad(conn, G, u)
-        sample = f"value+grad of the first {ne} tets of the {wl.a}^3 mesh per step"
+        G = mesh.G if wl.dtype == "f64" else mesh.G.astype("float32").astype("float64")
+        if wl.dtype == "f32":
+            u = u.astype("float32").astype("float64")
+        try:
+            cores = O.omp_threads()
+            conn = mesh.conn
+            unit_bytes = mesh.ne * (16 + 12 * wl.es) + 2 * mesh.nv * wl.es
+            fn = lambda: O.tet_grad_omp(conn, G, u)
+            sample = (f"full value+grad of the {wl.a}^3 mesh ({mesh.ne} tets) per step (oracle, "
+                      f"OpenMP build, {cores} threads)")
+        except Exception:  # noqa: BLE001  (no OpenMP build: serial oracle on 500k tets)
+            ne = min(mesh.ne, 500_000)
+            conn, G = mesh.conn[:ne], G[:ne]
+            unit_bytes = ne * (16 + 12 * wl.es) + 2 * mesh.nv * wl.es
+            fn = lambda: O.tet_grad(conn, G, u)
+            sample = f"value+grad of the first {ne} tets of the {wl.a}^3 mesh per step"
         to_value = lambda s: unit_bytes / 1e9 / s
     elif isinstance(wl, SparseWL):
         A, x = W.spquadform_inputs(wl.m)
@@ -1124,7 +1278,7 @@ def run_reference(args, rank, world):
            "scaling": "weak", "vs_baseline": None, "dtype": wl.dtype_name,
            "data": "synthetic (seeded numpy PCG64 draws)", "config": wl.config(),
            "impl": "reference",
-           "cpu_baseline": {"value": round(v, 5), "unit": wl.unit, "cores": 1, "kind": "oracle",
+           "cpu_baseline": {"value": round(v, 5), "unit": wl.unit, "cores": cores, "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": round(v, 5), "unit": wl.unit, "h2d_bytes_per_step": 0,
                    "d2h_bytes_per_step": 0}}

@@ -162,8 +162,20 @@ typedef struct {
 typedef struct kg_problem kg_problem;
 typedef struct kg_batch kg_batch;
 
-/* Fills *opt with defaults: KG_F64, AUTO strategy/mode/arith, check = 0. */
+/* Fills *opt with defaults: KG_F64, AUTO strategy/mode/arith, check = 0.
+ * No passage: library infrastructure. */
 void kg_options_default(kg_options *opt);
+
+/* Environment overrides, applied by kg_create on top of the caller's options
+ * (so a run can switch schedules without a rebuild):
+ *   KG_STRATEGY = auto | atomic | csr | transpose | fused | shared | warp
+ *   KG_MODE     = auto | recompute | tape
+ *   KG_ARITH    = auto | native | pair
+ *   KG_CHECK    = 0 | 1
+ * Unset or empty variables leave the field alone.  An unknown value returns
+ * KG_ERR_INVALID_ARG (message names the variable) and leaves *opt unchanged.
+ * Host only; usable without a GPU.  No passage: library infrastructure. */
+kg_status kg_options_apply_env(kg_options *opt);
 
 /* Create a problem (Sec. 3.1: shadow storage for every intermediate is
  * allocated once, here, never inside the per-call entry points).
@@ -182,11 +194,14 @@ void kg_options_default(kg_options *opt);
  * rowptr[m] = nnz, non-decreasing, columns in [0, n)) (KG_ERR_BOUNDS), builds
  * the transposed connectivity (tet CSR strategy) or the transposed matrix
  * (sparse TRANSPOSE strategy, values copied in column order), and synchronises
- * `s`. */
+ * `s`.  The environment overrides of kg_options_apply_env are applied to opt
+ * first. */
 kg_status kg_create(kg_problem **out, int kind, const int64_t *sizes, int nsizes,
                     const void *const *data, int ndata, const kg_options *opt, kg_stream s);
 
-/* Forward pass only: *f = f(x).  x: n (QUADFORM, SPQUADFORM, LAPLACE1D) or N_v (TET). */
+/* Forward pass only (the primal function: Sec. 4, Fig. "function_f", whose
+ * parallel_for / parallel_reduce kernels compute the value): *f = f(x).
+ * x: n (QUADFORM, SPQUADFORM, LAPLACE1D) or N_v (TET); f: device scalar. */
 kg_status kg_eval(kg_problem *p, const void *x, void *f, kg_stream s);
 
 /* Value and gradient (the paper's gradient function: forward pass, seed,
@@ -208,7 +223,9 @@ kg_status kg_grad(kg_problem *p, const void *x, void *f, void *gx, void *gdata,
  * intermediate y of the chain x -> y -> y^2 -> sum (LAPLACE1D).  f nullable. */
 kg_status kg_eval_tape(kg_problem *p, const void *x, void *f, kg_stream s);
 
-/* TAPE mode: reverse pass from the tape written by the last kg_eval_tape.
+/* TAPE mode: reverse pass from the tape as the last call that wrote it left
+ * it: kg_eval_tape, or (TET, CSR strategy) kg_grad, whose reverse pass goes
+ * through the same tape.  kg_tape_generation tells the two apart.
  * TET: gx[v] (+)= fbar * sum over incidences (e,k) of v of c_e[k], by atomic
  * scatter or by the CSR gather (the problem's strategy); reads no G.
  * LAPLACE1D: the reverse chain from y alone, ybar = 2 fbar y and
@@ -216,6 +233,14 @@ kg_status kg_eval_tape(kg_problem *p, const void *x, void *f, kg_stream s);
  * KG_ERR_STATE if no tape was recorded. */
 kg_status kg_grad_from_tape(kg_problem *p, void *gx, const void *seed, int accumulate,
                             kg_stream s);
+
+/* Number of launches so far that wrote the problem's tape (kg_eval_tape, and
+ * kg_grad of a TET problem with the CSR strategy).  A caller that records a
+ * tape and replays it later (e.g. an autograd backward) compares the value
+ * taken after its kg_eval_tape with the current one: if they differ, another
+ * call overwrote the tape in between and the reverse pass must recompute.
+ * Host-side counter; no synchronisation.  Tape restriction of Sec. 5. */
+kg_status kg_tape_generation(const kg_problem *p, uint64_t *gen);
 
 /* Hessian-vector product (forward mode over the reverse pass; the paper's
  * Sec. 5 lists forward mode as future work): hv (+)= fbar * H(x) v with H the
@@ -228,9 +253,10 @@ kg_status kg_grad_from_tape(kg_problem *p, void *gx, const void *seed, int accum
 kg_status kg_hvp(kg_problem *p, const void *x, const void *v, void *hv, const void *seed,
                  int accumulate, kg_stream s);
 
-/* End-to-end variant of kg_grad on HOST buffers: copies x (pageable or
- * pinned host memory) to the device, runs kg_grad with seed 1 on `s`, copies
- * f and gx back and synchronises `s`.  f_host nullable. */
+/* End-to-end variant of kg_grad on HOST buffers (the paper's gradient
+ * function returns its value to the host, Sec. 4, Fig. "grad_f"): copies x
+ * (pageable or pinned host memory) to the device, runs kg_grad with seed 1 on
+ * `s`, copies f and gx back and synchronises `s`.  f_host nullable. */
 kg_status kg_grad_host(kg_problem *p, const void *x_host, void *f_host, void *gx_host,
                        kg_stream s);
 
@@ -248,18 +274,23 @@ kg_status kg_grad_host(kg_problem *p, const void *x_host, void *f_host, void *gx
 kg_status kg_batch_create(kg_batch **out, kg_problem *const *probs, int count,
                           const kg_options *opt, kg_stream s);
 
-/* x[i], f[i], gx[i]: device pointers for instance i (f[i] nullable).  The
+/* Batched value and gradient in one launch (Sec. 5, second restriction: the
+ * gradient doubles the kernel launches and host synchronisation points, which
+ * fewer, larger launches avoid).
+ * x[i], f[i], gx[i]: device pointers for instance i (f[i] nullable).  The
  * pointer tables are host arrays of `count` entries; they are copied into the
  * batch's device table (a graph replay if unchanged since the last call). */
 kg_status kg_grad_batched(kg_batch *b, const void *const *x, void *const *f, void *const *gx,
                           kg_stream s);
 
 /* The batch's resolved FP64 arithmetic (kg_arith), number of work items in
- * its device table and persistent grid size.  Any pointer may be NULL. */
+ * its device table and persistent grid size.  Any pointer may be NULL.
+ * No passage: library infrastructure. */
 kg_status kg_batch_get_config(const kg_batch *b, int *arith, int *items, int *grid);
 
 /* Same work as kg_grad_batched, issued as one kg_grad launch sequence per
- * instance on `s` (the per-instance launch loop the batch is compared with). */
+ * instance on `s` (the per-instance launch loop the batch is compared with:
+ * the launch pattern Sec. 5, second restriction, describes). */
 kg_status kg_grad_batched_loop(kg_batch *b, const void *const *x, void *const *f,
                                void *const *gx, kg_stream s);
 
@@ -281,24 +312,57 @@ kg_status kg_grad_batched_loop(kg_batch *b, const void *const *x, void *const *f
 kg_status kg_quadform_grad_noalloc(const double *A, int64_t m, int64_t n, const double *x,
                                    double *f, double *gx, kg_stream s);
 
-/* Synchronises the problem's last stream and reads its sticky device error
- * word (cleared by the read): KG_ERR_BOUNDS, KG_ERR_TIMEOUT, KG_ERR_RANGE or
- * KG_OK. */
+/* Synchronises the problem's (batch's) last stream and reads its sticky
+ * device error word (cleared by the read): KG_ERR_BOUNDS, KG_ERR_TIMEOUT,
+ * KG_ERR_RANGE or KG_OK.  No passage: library infrastructure. */
 kg_status kg_sync(kg_problem *p);
 kg_status kg_batch_sync(kg_batch *b);
 
-/* Message for the last failure on this host thread ("" if none). */
+/* Check of the failure path of the bounded device waits: one warp waits,
+ * through the same bounded mbarrier wait the TMA pipelines use, on an
+ * mbarrier that nothing arrives at and no copy completes, with a limit of
+ * limit_ns nanoseconds (0 < limit_ns <= 2e9) instead of the kernels' one
+ * second.  The wait gives up, the kernel sets KG_ERR_TIMEOUT in the problem's
+ * sticky error word and returns normally (no copy is in flight, no trap), so
+ * the context stays usable; the next kg_sync returns KG_ERR_TIMEOUT.
+ * Asynchronous on `s`.  No passage: library infrastructure (failure
+ * detection of the waits every pipelined kernel uses). */
+kg_status kg_check_bounded_wait(kg_problem *p, uint64_t limit_ns, kg_stream s);
+
+/* Rates of this GPU that set the ALU rooflines of the native-FP64 kernels
+ * (and motivate the float-pair arithmetic), measured by small kernels of the
+ * library: eight independent register FMA chains per thread over 4 CTAs of
+ * 256 threads per SM (FP64, FP32), and red.global.add to pseudo-random slots
+ * of an 8 MiB array (FP64, FP32).  Best of three timed launches each, after a
+ * warm-up.  Allocates and frees an 8 MiB scratch array and synchronises `s`
+ * (a characterisation call, not a per-call entry point).  No passage: device
+ * characterisation for the roofline. */
+typedef struct {
+  double fp64_fma_tflops; /* FP64 FMA rate, 2 flops per FMA, 1e12 flop/s */
+  double fp32_fma_tflops; /* FP32 FMA rate, 1e12 flop/s */
+  double fp64_red_gops;   /* FP64 red.global.add to random L2-resident slots, 1e9/s */
+  double fp32_red_gops;   /* FP32 red.global.add, same pattern, 1e9/s */
+  int sms;                /* streaming multiprocessors */
+  int l2_bytes;           /* L2 cache size */
+} kg_box_rates;
+kg_status kg_measure_box(kg_box_rates *out, kg_stream s);
+
+/* Message for the last failure on this host thread ("" if none).
+ * No passage: library infrastructure. */
 const char *kg_last_error(void);
 
 /* The configuration kg_create resolved from the options (AUTO replaced by the
- * choice made): kg_strategy, kg_mode and kg_arith.  Any pointer may be NULL. */
+ * choice made): kg_strategy, kg_mode and kg_arith.  Any pointer may be NULL.
+ * No passage: library infrastructure. */
 kg_status kg_get_config(const kg_problem *p, int *strategy, int *mode, int *arith);
 
-/* Bytes of device workspace owned by the problem (tape, CSR, partials). */
+/* Bytes of device workspace owned by the problem (tape, CSR, partials).
+ * No passage: library infrastructure. */
 size_t kg_workspace_bytes(const kg_problem *p);
 
 /* Number of kernel launches the last per-call entry point issued on this
- * host thread (for launch accounting in benchmarks). */
+ * host thread (for launch accounting in benchmarks).
+ * No passage: library infrastructure. */
 int kg_last_launch_count(void);
 
 /* Main-kernel timing for benchmarks.  While enabled (on this host thread),
@@ -309,10 +373,12 @@ int kg_last_launch_count(void);
  * number of bracketed launches since the last kg_profile_enable(1); name
  * receives a static string naming the last bracketed kernel.  Up to 65536
  * launches are kept; later ones are not timed.  Not for use inside CUDA graph
- * capture. */
+ * capture.  No passage: library infrastructure. */
 kg_status kg_profile_enable(int on);
 kg_status kg_profile_read(double *ms, int *launches, const char **name);
 
+/* Free a problem's (batch's) workspaces; NULL is a no-op.  The borrowed
+ * inputs are not freed.  No passage: library infrastructure. */
 void kg_destroy(kg_problem *p);
 void kg_batch_destroy(kg_batch *b);
 

@@ -26,11 +26,11 @@ KG_MODE_AUTO, KG_MODE_RECOMPUTE, KG_MODE_TAPE = range(3)
 KG_ARITH_AUTO, KG_ARITH_NATIVE, KG_ARITH_PAIR = range(3)
 
 # Every symbol include/kg.h declares (checked by the test suite).
-EXPORTS = ["kg_options_default", "kg_create", "kg_eval", "kg_grad", "kg_eval_tape",
+EXPORTS = ["kg_options_default", "kg_options_apply_env", "kg_tape_generation", "kg_create", "kg_eval", "kg_grad", "kg_eval_tape",
            "kg_grad_from_tape", "kg_grad_host", "kg_batch_create", "kg_grad_batched",
            "kg_grad_batched_loop", "kg_batch_get_config", "kg_sync", "kg_batch_sync", "kg_last_error",
            "kg_get_config", "kg_workspace_bytes", "kg_last_launch_count", "kg_profile_enable", "kg_profile_read",
-           "kg_quadform_grad_noalloc", "kg_hvp", "kg_destroy", "kg_batch_destroy"]
+           "kg_quadform_grad_noalloc", "kg_hvp", "kg_check_bounded_wait", "kg_measure_box", "kg_destroy", "kg_batch_destroy"]
 
 
 class kg_options(ctypes.Structure):
@@ -38,6 +38,12 @@ class kg_options(ctypes.Structure):
                 ("arith", ctypes.c_int), ("check", ctypes.c_int), ("block", ctypes.c_int),
                 ("team", ctypes.c_int), ("tile", ctypes.c_int),
                 ("tape_budget_bytes", ctypes.c_size_t)]
+
+
+class kg_box_rates(ctypes.Structure):
+    _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
+                ("fp64_red_gops", ctypes.c_double), ("fp32_red_gops", ctypes.c_double),
+                ("sms", ctypes.c_int), ("l2_bytes", ctypes.c_int)]
 
 
 class KGError(RuntimeError):
@@ -66,6 +72,8 @@ def lib():
             vpp = ctypes.POINTER(ctypes.c_void_p)
             sig = {
                 "kg_options_default": (None, [optp]),
+                "kg_options_apply_env": (st, [optp]),
+                "kg_tape_generation": (st, [vp, ctypes.POINTER(ctypes.c_uint64)]),
                 "kg_create": (st, [ctypes.POINTER(vp), i, i64p, i, vpp, i, optp, vp]),
                 "kg_eval": (st, [vp, vp, vp, vp]),
                 "kg_grad": (st, [vp, vp, vp, vp, vp, vp, i, vp]),
@@ -87,6 +95,8 @@ def lib():
                 "kg_profile_read": (st, [ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                          ctypes.POINTER(ctypes.c_char_p)]),
                 "kg_quadform_grad_noalloc": (st, [vp, ctypes.c_int64, ctypes.c_int64, vp, vp, vp, vp]),
+                "kg_check_bounded_wait": (st, [vp, ctypes.c_uint64, vp]),
+                "kg_measure_box": (st, [ctypes.POINTER(kg_box_rates), vp]),
                 "kg_destroy": (None, [vp]),
                 "kg_batch_destroy": (None, [vp]),
             }
@@ -162,6 +172,28 @@ def kg_hvp(h, x, v, hv, seed=None, accumulate=0, stream=None):
 
 def kg_eval_tape(h, x, f=None, stream=None):
     check(lib().kg_eval_tape(h, ptr(x), ptr(f), stream_handle(stream)), "kg_eval_tape")
+
+
+def kg_options_apply_env(opt: kg_options) -> kg_options:
+    check(lib().kg_options_apply_env(ctypes.byref(opt)), "kg_options_apply_env")
+    return opt
+
+
+def kg_tape_generation(h) -> int:
+    g = ctypes.c_uint64()
+    check(lib().kg_tape_generation(h, ctypes.byref(g)), "kg_tape_generation")
+    return g.value
+
+
+def kg_measure_box(stream=None) -> dict:
+    """FP64/FP32 FMA and red rates, SM count and L2 size of the current GPU."""
+    r = kg_box_rates()
+    check(lib().kg_measure_box(ctypes.byref(r), stream_handle(stream)), "kg_measure_box")
+    return {k: getattr(r, k) for k, _ in kg_box_rates._fields_}
+
+
+def kg_check_bounded_wait(h, limit_ns: int, stream=None):
+    check(lib().kg_check_bounded_wait(h, int(limit_ns), stream_handle(stream)), "kg_check_bounded_wait")
 
 
 def kg_grad_from_tape(h, gx, seed=None, accumulate=0, stream=None):

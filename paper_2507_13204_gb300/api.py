@@ -131,8 +131,13 @@ class Problem:
         L.kg_eval_tape(self.handle, self._vec(x, "x"), f, stream)
         return f
 
+    @property
+    def tape_generation(self) -> int:
+        """Count of launches so far that wrote the tape (kg_tape_generation)."""
+        return L.kg_tape_generation(self.handle)
+
     def grad_from_tape(self, gx=None, seed=None, accumulate=False, stream=None):
-        """Reverse pass from the tape of the last eval_tape."""
+        """Reverse pass from the tape as the last call that wrote it left it."""
         gx = torch.empty(self.nx, dtype=self.dtype, device=self.device) if gx is None else self._vec(gx, "gx")
         L.kg_grad_from_tape(self.handle, gx, self._one(seed, "seed"), int(accumulate), stream)
         return gx

@@ -9,8 +9,11 @@ was created with a tape (mode "tape", or "auto" and the N_e x 4 tape fits the
 memory budget) the forward records c_e = G_e^T (2 g_e / (1 + |g_e|^2)) and the
 backward only scatters the tape (no G read, no FP64 math); otherwise the
 backward recomputes the forward inside the fused value-and-gradient kernel.
-A tape is valid only for the forward that wrote it: if another forward of the
-same problem ran in between, the backward recomputes instead.
+A tape is valid only for the forward that wrote it: the forward keeps the
+library's tape generation (kg_tape_generation, counted on the C side for every
+launch that writes the tape, including a CSR-strategy gradient, whose reverse
+pass goes through the same tape) and the backward recomputes if the count has
+moved since.
 
 KGQuadForm.apply(x, problem) does the same for f(x) = ||A x||^2 (recompute
 only: the reverse pass needs nothing but y, which the fused kernel rebuilds).
@@ -35,11 +38,10 @@ class KGTetEnergy(torch.autograd.Function):
             raise ValueError("KGTetEnergy: the problem was created without a tape")
         if use_tape:
             problem.eval_tape(u, f)
-            problem._tape_version = getattr(problem, "_tape_version", 0) + 1
-            ctx.tape_version = problem._tape_version
+            ctx.tape_gen = problem.tape_generation
         else:
             problem.eval(u, f)
-            ctx.tape_version = None
+            ctx.tape_gen = None
         ctx.save_for_backward(u)
         ctx.problem = problem
         return f
@@ -49,7 +51,7 @@ class KGTetEnergy(torch.autograd.Function):
         (u,) = ctx.saved_tensors
         problem = ctx.problem
         seed = grad_out.detach().to(dtype=u.dtype).contiguous()
-        if ctx.tape_version is not None and getattr(problem, "_tape_version", None) == ctx.tape_version:
+        if ctx.tape_gen is not None and problem.tape_generation == ctx.tape_gen:
             gu = problem.grad_from_tape(seed=seed)
         else:
             _, gu = problem.grad(u, seed=seed)

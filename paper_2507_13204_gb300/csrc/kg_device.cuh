@@ -135,12 +135,13 @@ __device__ __forceinline__ uint64_t global_ns() {
 constexpr uint64_t kWaitLimitNs = 1000000000ull;
 // The clock is read on every 64th failed try only: spinning warps then issue
 // little besides the try-wait itself.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   for (uint32_t i = 1;; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
-    if ((i & 63u) == 0u && global_ns() - t0 > kWaitLimitNs) return false;
+    if ((i & 63u) == 0u && global_ns() - t0 > limit_ns) return false;
   }
 }
 

@@ -73,6 +73,7 @@ struct kg_problem {
   void* tape = nullptr;      // tet: c_e [N_e][4]
   void* aprep = nullptr;     // FP64 pair: A (dense) or G (tet) split into float pairs
   bool tape_valid = false;
+  uint64_t tape_gen = 0;     // launches that wrote the tape (kg_tape_generation)
   int* rowptr = nullptr;     // tet CSR: [N_v + 1]; sparse CSC: colptr [n + 1]
   int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k; sparse CSC: row of each entry
   void* valT = nullptr;      // sparse CSC: values in column order

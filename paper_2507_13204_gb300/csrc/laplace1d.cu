@@ -278,6 +278,7 @@ static kg_status lap_eval_tape_t(kg_problem* p, const void* x, void* f, cudaStre
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "1-D taping forward kernel");
   p->tape_valid = true;
+  p->tape_gen += 1;
   return KG_OK;
 }
 

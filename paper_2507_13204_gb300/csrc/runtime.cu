@@ -12,9 +12,24 @@
 #include <string>
 #include <vector>
 
+#include "kg_device.cuh"
 #include "kg_internal.h"
 
 namespace kg {
+
+// One warp waits, through the same bounded wait as the TMA pipelines, on an
+// mbarrier that nothing arrives at and no copy completes: the wait gives up
+// after limit_ns, the kernel records ERRBIT_TIMEOUT and returns normally.
+__global__ void bounded_wait_check_kernel(uint64_t limit_ns, unsigned* err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    fence_barrier_init();
+  }
+  __syncwarp();
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+  if (!__all_sync(0xffffffffu, ok) && threadIdx.x == 0) set_error(err, ERRBIT_TIMEOUT);
+}
 
 static thread_local std::string t_msg;
 static thread_local int t_launches = 0;
@@ -141,6 +156,47 @@ void kg_options_default(kg_options* o) {
 
 const char* kg_last_error(void) { return t_msg.c_str(); }
 
+static int env_choice(const char* name, const char* const* words, const int* values, int count,
+                      int* out) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return 0;
+  for (int i = 0; i < count; ++i)
+    if (std::strcmp(v, words[i]) == 0) {
+      *out = values[i];
+      return 0;
+    }
+  std::string allowed;
+  for (int i = 0; i < count; ++i) allowed += (i ? "|" : "") + std::string(words[i]);
+  fail(KG_ERR_INVALID_ARG, std::string(name) + "=" + v + ": expected one of " + allowed);
+  return -1;
+}
+
+kg_status kg_options_apply_env(kg_options* o) {
+  if (!o) return fail(KG_ERR_INVALID_ARG, "kg_options_apply_env: NULL options");
+  static const char* const sw[] = {"auto", "atomic", "csr", "transpose", "fused", "shared", "warp"};
+  static const int sv[] = {KG_STRATEGY_AUTO, KG_STRATEGY_ATOMIC, KG_STRATEGY_CSR,
+                           KG_STRATEGY_TRANSPOSE, KG_STRATEGY_FUSED, KG_STRATEGY_SHARED,
+                           KG_STRATEGY_WARP};
+  static const char* const mw[] = {"auto", "recompute", "tape"};
+  static const int mv[] = {KG_MODE_AUTO, KG_MODE_RECOMPUTE, KG_MODE_TAPE};
+  static const char* const aw[] = {"auto", "native", "pair"};
+  static const int av[] = {KG_ARITH_AUTO, KG_ARITH_NATIVE, KG_ARITH_PAIR};
+  static const char* const cw[] = {"0", "1"};
+  static const int cv[] = {0, 1};
+  kg_options r = *o;
+  if (env_choice("KG_STRATEGY", sw, sv, 7, &r.strategy) || env_choice("KG_MODE", mw, mv, 3, &r.mode) ||
+      env_choice("KG_ARITH", aw, av, 3, &r.arith) || env_choice("KG_CHECK", cw, cv, 2, &r.check))
+    return KG_ERR_INVALID_ARG;
+  *o = r;
+  return KG_OK;
+}
+
+kg_status kg_tape_generation(const kg_problem* p, uint64_t* gen) {
+  if (!p || !gen) return fail(KG_ERR_INVALID_ARG, "kg_tape_generation: NULL argument");
+  *gen = p->tape_gen;
+  return KG_OK;
+}
+
 int kg_last_launch_count(void) { return t_launches; }
 
 kg_status kg_profile_enable(int on) {
@@ -191,6 +247,7 @@ kg_status kg_create(kg_problem** out, int kind, const int64_t* sizes, int nsizes
   kg_options o;
   kg_options_default(&o);
   if (opt) o = *opt;
+  if (kg_options_apply_env(&o) != KG_OK) return KG_ERR_INVALID_ARG;
   if (o.dtype != KG_F64 && o.dtype != KG_F32)
     return fail(KG_ERR_INVALID_ARG, "kg_create: dtype must be KG_F64 or KG_F32");
   if (o.strategy < KG_STRATEGY_AUTO || o.strategy > KG_STRATEGY_WARP)
@@ -423,6 +480,20 @@ kg_status kg_sync(kg_problem* p) {
   if (h & ERRBIT_TIMEOUT) return fail(KG_ERR_TIMEOUT, "device: a bounded wait gave up");
   if (h & ERRBIT_RANGE)
     return fail(KG_ERR_RANGE, "device: an input is outside the float-pair range (0 or 2^-60 <= |v| < 2^40)");
+  return KG_OK;
+}
+
+kg_status kg_check_bounded_wait(kg_problem* p, uint64_t limit_ns, kg_stream s) {
+  reset_launch_count();
+  if (!p || !p->err) return fail(KG_ERR_INVALID_ARG, "kg_check_bounded_wait: NULL problem");
+  if (limit_ns == 0 || limit_ns > 2000000000ull)
+    return fail(KG_ERR_INVALID_ARG, "kg_check_bounded_wait: limit_ns must be in (0, 2e9]");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(s);
+  p->last_stream = st;
+  bounded_wait_check_kernel<<<1, 32, 0, st>>>(limit_ns, p->err);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "kg_check_bounded_wait");
   return KG_OK;
 }
 

@@ -436,7 +436,10 @@ static kg_status tet_direct(kg_problem* p, int mode, const void* x, const void* 
 kg_status tet_eval(kg_problem* p, const void* x, void* f, bool tape, cudaStream_t s) {
   kg_status rc = use_direct(p) ? tet_direct(p, tape ? TS_TAPE : TS_EVAL, x, nullptr, f, nullptr, nullptr, s)
                                : tet_staged(p, tape ? 2 : 0, x, f, nullptr, nullptr, s);
-  if (rc == KG_OK && tape) p->tape_valid = true;
+  if (rc == KG_OK && tape) {
+    p->tape_valid = true;
+    p->tape_gen += 1;
+  }
   return rc;
 }
 

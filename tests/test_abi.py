@@ -83,3 +83,35 @@ def test_binding_raises_with_message(lib):
     with pytest.raises(L.KGError) as ei:
         L.check(lib.kg_eval(None, None, None, None), "kg_eval")
     assert ei.value.status == L.KG_ERR_INVALID_ARG and "NULL" in str(ei.value)
+
+
+def test_environment_overrides_of_the_options(lib, monkeypatch):
+    for var in ("KG_STRATEGY", "KG_MODE", "KG_ARITH", "KG_CHECK"):
+        monkeypatch.delenv(var, raising=False)
+    o = L.options()
+    L.kg_options_apply_env(o)  # nothing set: unchanged
+    assert (o.strategy, o.mode, o.arith, o.check) == (0, 0, 0, 0)
+    monkeypatch.setenv("KG_STRATEGY", "csr")
+    monkeypatch.setenv("KG_MODE", "tape")
+    monkeypatch.setenv("KG_ARITH", "native")
+    monkeypatch.setenv("KG_CHECK", "1")
+    L.kg_options_apply_env(o)
+    assert (o.strategy, o.mode, o.arith, o.check) == (L.KG_STRATEGY_CSR, L.KG_MODE_TAPE,
+                                                      L.KG_ARITH_NATIVE, 1)
+    monkeypatch.setenv("KG_MODE", "sometimes")
+    before = (o.strategy, o.mode, o.arith, o.check)
+    with pytest.raises(L.KGError) as ei:
+        L.kg_options_apply_env(o)
+    assert ei.value.status == L.KG_ERR_INVALID_ARG and "KG_MODE" in str(ei.value)
+    assert (o.strategy, o.mode, o.arith, o.check) == before
+    # kg_create applies them before it touches the device: a bad value is rejected first
+    h = ctypes.c_void_p()
+    sz = (ctypes.c_int64 * 1)(8)
+    data = (ctypes.c_void_p * 1)(16)
+    assert lib.kg_create(ctypes.byref(h), L.KG_QUADFORM, sz, 1, data, 1, None, None) == L.KG_ERR_INVALID_ARG
+    assert "KG_MODE" in lib.kg_last_error().decode()
+
+
+def test_tape_generation_rejects_null(lib):
+    g = ctypes.c_uint64(7)
+    assert lib.kg_tape_generation(None, ctypes.byref(g)) == L.KG_ERR_INVALID_ARG

@@ -10,6 +10,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 import bench  # noqa: E402
+from oracle import oracle as O  # noqa: E402
 
 
 def test_traffic_reported_only_at_default_sizes_and_matching_fingerprint():
@@ -76,5 +77,18 @@ def _host_workload(name):
 
 @pytest.mark.parametrize("name", ["dense", "sparse", "laplace", "batched", "tet", "hvp", "autograd"])
 def test_cpu_baseline_legs_run_on_host_data(name):
-    value, sample = _host_workload(name).oracle_sample(budget_s=0.05)
-    assert value > 0 and "oracle" in sample
+    res = _host_workload(name).oracle_sample(budget_s=0.05)
+    if isinstance(res, dict):  # dense and tet: the OpenMP build on all cores, serial beside it
+        assert res["value"] > 0 and "oracle" in res["sample"] and res["kind"] == "oracle"
+        assert res["cores"] == O.omp_threads() >= 1
+        assert res["single_thread"]["cores"] == 1 and res["single_thread"]["value"] > 0
+    else:
+        value, sample = res
+        assert value > 0 and "oracle" in sample
+
+
+def test_fp64_peak_prefers_the_measured_rate():
+    peaks = {"fp64_tflops": 1.258}
+    assert bench.fp64_peak(peaks, {"fp64_fma_tflops": 1.19})[0] == 1.19
+    assert bench.fp64_peak(peaks, {"error": "x"})[0] == 1.258
+    assert bench.fp64_peak(peaks, None)[0] == 1.258

@@ -74,6 +74,33 @@ def test_stale_tape_falls_back_to_recompute(mods):
     assert rel_l2(u2.grad.cpu().numpy(), g2) <= TOL["f64"]
 
 
+def test_csr_gradient_between_tape_forward_and_backward(mods):
+    """A CSR-strategy gradient writes the same tape as a taping forward (its
+    reverse pass gathers from it).  A forward on the tape path, then a direct
+    gradient and a recompute-policy forward/backward at another point, then the
+    first backward: the first backward must see that its tape was overwritten
+    (the library's tape generation moved) and recompute at its own point."""
+    api, ag = mods
+    mesh = W.tet_mesh(5, jitter_seed=2, perm_seed=4)
+    p = _tet(api, mesh, strategy="csr", mode="tape")
+    rng = np.random.default_rng(12)
+    u1 = torch.tensor(rng.uniform(-1, 1, mesh.nv), device="cuda", requires_grad=True)
+    u2 = torch.tensor(rng.uniform(-1, 1, mesh.nv), device="cuda", requires_grad=True)
+    g0 = p.tape_generation
+    f1 = ag.KGTetEnergy.apply(u1, p)  # tape path: records the tape at u1
+    assert p.tape_generation == g0 + 1
+    _, gd = p.grad(u2.detach())       # CSR gradient at u2: rewrites the tape
+    assert p.tape_generation == g0 + 2
+    f2 = ag.KGTetEnergy.apply(u2, p, "recompute")
+    f2.backward()
+    f1.backward()
+    _, g1 = O.tet_grad(mesh.conn, mesh.G, u1.detach().cpu().numpy())
+    _, g2 = O.tet_grad(mesh.conn, mesh.G, u2.detach().cpu().numpy())
+    assert rel_l2(u1.grad.cpu().numpy(), g1) <= TOL["f64"]
+    assert rel_l2(u2.grad.cpu().numpy(), g2) <= TOL["f64"]
+    assert rel_l2(gd.cpu().numpy(), g2) <= TOL["f64"]
+
+
 def test_quadform_function_gradcheck(mods):
     api, ag = mods
     A, x = W.quadform_inputs(20, m=13, seed=2)

@@ -62,3 +62,44 @@ def test_misaligned_data_rejected(mods):
     with pytest.raises(L.KGError) as ei:
         kg_create(KG_QUADFORM, [4, 4], [buf.data_ptr() + 8])
     assert ei.value.status == L.KG_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("limit_us", [50, 2000])
+def test_bounded_wait_runs_out_and_reports_timeout(mods, limit_us):
+    """A device wait whose barrier nothing completes gives up after its limit:
+    the kernel records KG_ERR_TIMEOUT and returns, kg_sync reports it (and
+    clears it), and the context stays usable for a correct gradient after."""
+    import time
+
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2507_13204_gb300 import workloads as W
+    L, A = mods
+    Ah, xh = W.quadform_inputs(96, m=40, seed=5)
+    p = A.QuadForm(torch.tensor(Ah, device="cuda"))
+    p.sync()
+    t0 = time.perf_counter()
+    L.kg_check_bounded_wait(p.handle, limit_us * 1000)
+    with pytest.raises(L.KGError) as ei:
+        p.sync()
+    elapsed = time.perf_counter() - t0
+    assert ei.value.status == L.KG_ERR_TIMEOUT
+    assert "gave up" in str(ei.value)
+    assert elapsed >= limit_us * 1e-6
+    p.sync()  # the read cleared the sticky word
+    f, g = p.grad(torch.tensor(xh, device="cuda"))
+    p.sync()
+    f_ref, g_ref = O.quadform_grad(Ah, xh)
+    assert abs(f.item() - f_ref) <= 1e-12 * abs(f_ref)
+    assert np.linalg.norm(g.cpu().numpy() - g_ref) <= 1e-12 * np.linalg.norm(g_ref)
+    p.close()
+
+
+def test_bounded_wait_check_rejects_bad_limits(mods):
+    L, A = mods
+    p = A.QuadForm(torch.zeros((4, 4), dtype=torch.float64, device="cuda"))
+    for bad in (0, 3_000_000_000):
+        with pytest.raises(L.KGError) as ei:
+            L.kg_check_bounded_wait(p.handle, bad)
+        assert ei.value.status == L.KG_ERR_INVALID_ARG
+    p.close()
