@@ -260,6 +260,12 @@ __global__ void __launch_bounds__(QP_THREADS, 1) qf_pair_kernel(QpArgs a) {
 // first chunk was refilled, i.e. after the update warps read row i's partials,
 // so the two-row partial buffer and each y-ready barrier are never more than
 // one phase ahead.  All waits are bounded and report KG_ERR_TIMEOUT.
+// The ring starts zeroed and a copy fills only the first n/2 - H pairs of a
+// row's second chunk, so every slot holds zeros or finite entries of A beyond
+// the row's end: the loops read there without a bounds test (x is zero there,
+// and the xbar entries past the row's end are never stored).  Only the dot
+// warps' last column pair can reach past the second chunk's slot; it keeps its
+// test.
 constexpr int WS_DW = 7, WS_UW = 8;             // dot and update warps
 constexpr int WS_THREADS = (WS_DW + WS_UW + 1) * 32;
 constexpr int WS_SLOTS = 5;
@@ -294,6 +300,8 @@ __global__ void __launch_bounds__(WS_THREADS, 1) qf_pair_ws_kernel(QpArgs a) {
     *abort_flag = 0;
     fence_barrier_init();
   }
+  for (int i = threadIdx.x; i < WS_SLOTS * H; i += WS_THREADS) slots[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  fence_proxy_async_smem();  // the zeros are written before any copy lands in the ring
   __syncthreads();
 
   if (warp < WS_DW) {
@@ -330,7 +338,7 @@ __global__ void __launch_bounds__(WS_THREADS, 1) qf_pair_ws_kernel(QpArgs a) {
 #pragma unroll
       for (int k = 0; k < KPD; ++k) {
         const int jp = t + TD * k;
-        if (jp < npairs) {
+        if (TD * (k + 1) <= 2 * H || jp < 2 * H) {  // the test is compiled for the last k only
           const float4 q = jp < H ? buf0[jp] : buf1[jp - H];
           acc_fma(yc[2 * (k & 1)], q.x, q.y, xh[k][0], xl[k][0]);
           acc_fma(yc[2 * (k & 1) + 1], q.z, q.w, xh[k][1], xl[k][1]);
@@ -382,11 +390,9 @@ __global__ void __launch_bounds__(WS_THREADS, 1) qf_pair_ws_kernel(QpArgs a) {
 #pragma unroll
           for (int kk = 0; kk < KP / 2; ++kk) {
             const int k = c * (KP / 2) + kk;
-            if (t + TU * k < npairs) {
-              const float4 q = buf[t + TU * kk];
-              acc_fma(xb[k][0], q.x, q.y, yb.h, yb.l);
-              acc_fma(xb[k][1], q.z, q.w, yb.h, yb.l);
-            }
+            const float4 q = buf[t + TU * kk];
+            acc_fma(xb[k][0], q.x, q.y, yb.h, yb.l);
+            acc_fma(xb[k][1], q.z, q.w, yb.h, yb.l);
           }
         }
         __syncwarp();

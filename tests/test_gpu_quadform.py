@@ -210,11 +210,14 @@ def test_pair_exact_cases(api):
     assert rel_l2(g.cpu().numpy(), g_ref) <= 2e-14
 
 
-@pytest.mark.parametrize("m,n", [(1, 2050), (77, 4098), (200, 6146), (151, 8194), (500, 10240)])
+@pytest.mark.parametrize("m,n", [(1, 2050), (77, 4098), (200, 6146), (151, 8194), (500, 10240),
+                                 (3000, 4098), (2600, 10000)])
 def test_warp_specialized_fused_kernel_shapes(api, m, n):
-    # 2048 < n <= 10240 on the prepared A runs the warp-specialized fused kernel: every
-    # chunk width (column pairs per update thread 8, 12, 16, 20), a single row, ragged row
-    # counts per CTA; a seed, and the same result on a second call
+    # 2048 < n <= 10240 on the prepared A runs the warp-specialized fused kernel in 2-CTA
+    # clusters: every chunk width (2..5 column pairs per role thread and chunk), odd pair
+    # counts (the two CTAs' column halves differ by one pair), a single row, ragged row
+    # counts per cluster, bands of more than 16 and 32 rows (the partial buffer and the
+    # chunk ring wrap around); a seed, and the same result on a second call
     A, x = W.quadform_inputs(n, m=m, seed=m + n)
     f_ref, g_ref = O.quadform_grad(A, x, fbar=0.5)
     p = api.QuadForm(torch.tensor(A, device="cuda"))
