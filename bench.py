@@ -881,7 +881,7 @@ def main():
                     help="problem size override (dense n, tet cubes per axis, 1-D n) for small "
                          "profiling cases; the default is the full workload")
     ap.add_argument("--rows", type=int, default=0, help="dense: rows of A (default: square)")
-    ap.add_argument("--strategy", default="", choices=["", "atomic", "shared", "warp", "csr",
+    ap.add_argument("--strategy", default="", choices=["", "atomic", "shared", "warp", "tile", "csr",
                                                        "transpose"],
                     help="tet, batched, sparse: reverse-pass scatter strategy (default: the "
                          "library's choice)")

@@ -106,8 +106,18 @@ typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
  *             atomic.  FP64 data combines runs of consecutive lanes (elements
  *             numbered along the mesh); FP32 data combines equal vertices
  *             anywhere in the warp.  The result holds for any element order.
- *   AUTO      FUSED for dense, WARP for tets, ATOMIC for sparse, the stencil
- *             transpose for 1-D. */
+ *   TILE      (tet) the reverse pass rescheduled per tile of 32 consecutive
+ *             elements (Sec. 5: rescheduling the reverse pass): kg_create
+ *             sorts each tile's 128 incidences by vertex, giving the tile's
+ *             distinct vertices and their incidence lists; the gradient
+ *             stores a warp's 32 element adjoints in shared memory, then one
+ *             lane per tile vertex adds its incidences in ascending order and
+ *             issues one global atomic.  Value-and-gradient and Hessian-vector
+ *             products; FP32, or FP64 in PAIR arithmetic with the prepared G;
+ *             no bounds checks (else KG_ERR_UNSUPPORTED).
+ *   AUTO      FUSED for dense; for tets TILE with FP32 data (no bounds checks)
+ *             and WARP otherwise; ATOMIC for sparse; the stencil transpose for
+ *             1-D. */
 typedef enum {
   KG_STRATEGY_AUTO = 0,
   KG_STRATEGY_ATOMIC = 1,
@@ -115,7 +125,8 @@ typedef enum {
   KG_STRATEGY_TRANSPOSE = 3,
   KG_STRATEGY_FUSED = 4,
   KG_STRATEGY_SHARED = 5,
-  KG_STRATEGY_WARP = 6
+  KG_STRATEGY_WARP = 6,
+  KG_STRATEGY_TILE = 7
 } kg_strategy;
 
 /* Forward values for the reverse pass (Sec. 5, taping restriction).
@@ -168,7 +179,7 @@ void kg_options_default(kg_options *opt);
 
 /* Environment overrides, applied by kg_create on top of the caller's options
  * (so a run can switch schedules without a rebuild):
- *   KG_STRATEGY = auto | atomic | csr | transpose | fused | shared | warp
+ *   KG_STRATEGY = auto | atomic | csr | transpose | fused | shared | warp | tile
  *   KG_MODE     = auto | recompute | tape
  *   KG_ARITH    = auto | native | pair
  *   KG_CHECK    = 0 | 1

@@ -21,7 +21,7 @@ STATUS_NAMES = ["KG_OK", "KG_ERR_INVALID_ARG", "KG_ERR_OOM", "KG_ERR_CUDA", "KG_
 KG_QUADFORM, KG_TETENERGY, KG_LAPLACE1D, KG_SPQUADFORM = 1, 2, 3, 4
 KG_F64, KG_F32 = 0, 1
 KG_STRATEGY_AUTO, KG_STRATEGY_ATOMIC, KG_STRATEGY_CSR, KG_STRATEGY_TRANSPOSE, KG_STRATEGY_FUSED, \
-    KG_STRATEGY_SHARED, KG_STRATEGY_WARP = range(7)
+    KG_STRATEGY_SHARED, KG_STRATEGY_WARP, KG_STRATEGY_TILE = range(8)
 KG_MODE_AUTO, KG_MODE_RECOMPUTE, KG_MODE_TAPE = range(3)
 KG_ARITH_AUTO, KG_ARITH_NATIVE, KG_ARITH_PAIR = range(3)
 
@@ -253,7 +253,7 @@ def kg_get_config(h):
     """Resolved (strategy, mode, arith) names of a problem."""
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     check(lib().kg_get_config(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "kg_get_config")
-    strat = ["auto", "atomic", "csr", "transpose", "fused", "shared", "warp"][a.value]
+    strat = ["auto", "atomic", "csr", "transpose", "fused", "shared", "warp", "tile"][a.value]
     return strat, ["auto", "recompute", "tape"][b.value], ["auto", "native", "pair"][c.value]
 
 

@@ -13,7 +13,7 @@ from . import _lib as L
 _DT = {torch.float64: L.KG_F64, torch.float32: L.KG_F32}
 STRATEGIES = {"auto": L.KG_STRATEGY_AUTO, "atomic": L.KG_STRATEGY_ATOMIC, "csr": L.KG_STRATEGY_CSR,
               "transpose": L.KG_STRATEGY_TRANSPOSE, "fused": L.KG_STRATEGY_FUSED,
-              "shared": L.KG_STRATEGY_SHARED, "warp": L.KG_STRATEGY_WARP}
+              "shared": L.KG_STRATEGY_SHARED, "warp": L.KG_STRATEGY_WARP, "tile": L.KG_STRATEGY_TILE}
 MODES = {"auto": L.KG_MODE_AUTO, "recompute": L.KG_MODE_RECOMPUTE, "tape": L.KG_MODE_TAPE}
 ARITHS = {"auto": L.KG_ARITH_AUTO, "native": L.KG_ARITH_NATIVE, "pair": L.KG_ARITH_PAIR}
 

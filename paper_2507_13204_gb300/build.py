@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libkg.so")
 SOURCES = ["runtime.cu", "quadform.cu", "quadform_pair.cu", "quadform_f32.cu", "tet.cu", "tet_pair.cu",
-           "laplace1d.cu", "batched.cu", "noalloc.cu", "spquadform.cu", "box.cu"]
+           "laplace1d.cu", "batched.cu", "noalloc.cu", "spquadform.cu", "box.cu",
+           "tet_tile.cu"]
 HEADERS = ["kg_internal.h", "kg_device.cuh", "kg_pair.cuh", "kg_tet_elem.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",

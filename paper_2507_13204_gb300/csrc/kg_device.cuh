@@ -145,6 +145,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// In a kernel launched with programmatic stream serialization: blocks until
+// the preceding grid on the stream has completed and its memory operations
+// are visible (returns at once otherwise).
+__device__ __forceinline__ void grid_dependency_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 // Global floating-point add whose old value is not wanted: PTX red (a
 // reduction at L2 that returns nothing to the SM), where atomicAdd's atom form
 // also brings the old value back.  p points to global memory.

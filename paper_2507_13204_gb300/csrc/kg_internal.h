@@ -78,6 +78,13 @@ struct kg_problem {
   int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k; sparse CSC: row of each entry
   void* valT = nullptr;      // sparse CSC: values in column order
   void* usplit = nullptr;    // tet pair: u and v as float pairs [2][N_v], split per call
+  // tet TILE strategy (tet_tile.cu): per tile of 32 elements, its distinct
+  // vertices and their incidence lists, built at kg_create
+  int* tile_nv = nullptr;
+  int* tile_vlist = nullptr;
+  uint8_t* tile_vptr = nullptr;
+  uint8_t* tile_inc = nullptr;
+  int ntiles = 0;
   void* xdev = nullptr;      // kg_grad_host staging
   void* gdev = nullptr;
   void* fdev = nullptr;
@@ -138,6 +145,21 @@ kg_status tet_grad_from_tape(kg_problem* p, void* gx, const void* seed, int accu
                              cudaStream_t s);
 kg_status tet_hvp(kg_problem* p, const void* x, const void* v, void* hv, const void* seed,
                   int accumulate, cudaStream_t s);
+
+// tiled reverse pass (tet_tile.cu): whether it applies, its create-time build,
+// and one value-and-gradient (mode TS_GRAD) or Hessian-vector product (TS_HVP)
+// from the float pairs of u (and v) split this call
+bool tet_tile_supported(const kg_problem* p);
+kg_status tet_tile_setup(kg_problem* p, cudaStream_t s);
+kg_status tet_tile_run(kg_problem* p, int mode, const float2* us, const float2* vs, void* f, void* gx,
+                       const void* seed, cudaStream_t s);
+kg_status tet_tile_run_f32(kg_problem* p, int mode, const void* x, const void* v, void* f, void* gx,
+                           const void* seed, cudaStream_t s);
+// u (and v) of a float-pair tet problem split into float pairs in the
+// problem's workspace, gx zeroed when zero_gx (tet_pair.cu); *us / *vs receive
+// the pairs
+kg_status tet_split_vertex_values(kg_problem* p, const void* x, const void* v, void* gx, bool zero_gx,
+                                  const float2** us, const float2** vs, cudaStream_t s);
 
 // Buckets of positions by key (transposed index lists; tet.cu), synchronises s.
 kg_status build_buckets(const int* keys, int64_t count, int nbins, int* binptr, int* perm,

@@ -213,6 +213,44 @@ __device__ __forceinline__ void elem_native(const int4 c, const T* __restrict__ 
   }
 }
 
+// The arithmetic of one element in float pairs, from its G_e (12 pairs) and
+// gathered vertex values U (4 pairs): g = G_e u_e, f_e = log1p(|g|^2) added to
+// facc, and (MODE != TS_EVAL) the element adjoint
+// cp[k] = (G_e^T (2 fbar g / (1 + |g|^2)))_k, with fb2 = 2 fbar as a pair.
+template <int MODE>
+__device__ __forceinline__ void elem_pair_core(const Pair (&G)[12], const Pair (&U)[4], Pair fb2,
+                                               const float4* __restrict__ tab, const LogConsts& K,
+                                               Acc& facc, Pair (&cp)[4]) {
+  Pair g[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    Acc a = acc_prod(G[4 * r].h, G[4 * r].l, U[0].h, U[0].l);
+#pragma unroll
+    for (int k = 1; k < 4; ++k) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, U[k].h, U[k].l);
+    g[r] = acc_pair(a);
+  }
+  Acc sa = acc_prod(g[0].h, g[0].l, g[0].h, g[0].l);
+#pragma unroll
+  for (int r = 1; r < 3; ++r) acc_fma(sa, g[r].h, g[r].l, g[r].h, g[r].l);
+  const Pair s = acc_pair(sa);
+  Pair t;
+  const Pair lf = pair_log1p(s, tab, K, t);
+  facc = acc_add(facc, Acc{lf.h, lf.l});
+  if constexpr (MODE != TS_EVAL) {
+    const Pair w = pair_mul(fb2, pair_recip(t));
+    Pair wg[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) wg[r] = pair_mul(w, g[r]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Acc a = acc_prod(G[k].h, G[k].l, wg[0].h, wg[0].l);
+#pragma unroll
+      for (int r = 1; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, wg[r].h, wg[r].l);
+      cp[k] = acc_pair(a);
+    }
+  }
+}
+
 // One element in float-pair arithmetic (FP64 data).  Gs points at the
 // element's 12 doubles, or (PREP) at its 12 float pairs (h, l) prepared once.
 // USPLIT: u points at float pairs of the vertex values, split (and range
@@ -251,34 +289,9 @@ __device__ __forceinline__ void elem_pair(const int4 c, const double* __restrict
       U[k] = split_f64(ud[k]);
     }
   }
-  Pair g[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    Acc a = acc_prod(G[4 * r].h, G[4 * r].l, U[0].h, U[0].l);
-#pragma unroll
-    for (int k = 1; k < 4; ++k) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, U[k].h, U[k].l);
-    g[r] = acc_pair(a);
-  }
-  Acc sa = acc_prod(g[0].h, g[0].l, g[0].h, g[0].l);
-#pragma unroll
-  for (int r = 1; r < 3; ++r) acc_fma(sa, g[r].h, g[r].l, g[r].h, g[r].l);
-  const Pair s = acc_pair(sa);
-  Pair t;
-  const Pair lf = pair_log1p(s, tab, K, t);
-  facc = acc_add(facc, Acc{lf.h, lf.l});
+  Pair cp[4];
+  elem_pair_core<MODE>(G, U, fb2, tab, K, facc, cp);
   if constexpr (MODE != TS_EVAL) {
-    const Pair w = pair_mul(fb2, pair_recip(t));
-    Pair wg[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) wg[r] = pair_mul(w, g[r]);
-    Pair cp[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      Acc a = acc_prod(G[k].h, G[k].l, wg[0].h, wg[0].l);
-#pragma unroll
-      for (int r = 1; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, wg[r].h, wg[r].l);
-      cp[k] = acc_pair(a);
-    }
     if constexpr (MODE == TS_GRAD) {
       sink_pair(gu, 0, c.x, cp[0]);
       sink_pair(gu, 1, c.y, cp[1]);
@@ -327,41 +340,10 @@ __device__ __forceinline__ void elem_native_hvp(const int4 c, const T* __restric
   gu(3, c.w, G[3] * h[0] + G[7] * h[1] + G[11] * h[2]);
 }
 
-// The same in float-pair arithmetic (FP64 data); fb2 = 2 fbar as a pair.
-template <typename Sink, bool PREP = false, bool USPLIT = false>
-__device__ __forceinline__ void elem_pair_hvp(const int4 c, const double* __restrict__ Gs,
-                                              const double* __restrict__ u,
-                                              const double* __restrict__ v, Pair fb2,
-                                              const Sink& gu, bool& bad) {
-  Pair G[12];
-#pragma unroll
-  for (int i = 0; i < 12; i += 2) {
-    if constexpr (PREP) {
-      const float4 q = *reinterpret_cast<const float4*>(Gs + i);
-      G[i] = Pair{q.x, q.y};
-      G[i + 1] = Pair{q.z, q.w};
-    } else {
-      const double2 q = *reinterpret_cast<const double2*>(Gs + i);
-      G[i] = split_f64(q.x);
-      G[i + 1] = split_f64(q.y);
-    }
-  }
-  const int idx[4] = {c.x, c.y, c.z, c.w};
-  Pair U[4], V[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if constexpr (USPLIT) {
-      const float2 qu = __ldg(reinterpret_cast<const float2*>(u) + idx[k]);
-      const float2 qv = __ldg(reinterpret_cast<const float2*>(v) + idx[k]);
-      U[k] = Pair{qu.x, qu.y};
-      V[k] = Pair{qv.x, qv.y};
-    } else {
-      const double uk = __ldg(u + idx[k]), vk = __ldg(v + idx[k]);
-      bad |= !pair_in_range(uk) || !pair_in_range(vk);
-      U[k] = split_f64(uk);
-      V[k] = split_f64(vk);
-    }
-  }
+// The Hessian-vector arithmetic of one element in float pairs, from its G_e
+// and the gathered U (point) and V (direction): hc[k] = (G_e^T (wd g + w gd))_k.
+__device__ __forceinline__ void elem_pair_hvp_core(const Pair (&G)[12], const Pair (&U)[4],
+                                                   const Pair (&V)[4], Pair fb2, Pair (&hc)[4]) {
   Pair g[3], gd[3];
 #pragma unroll
   for (int r = 0; r < 3; ++r) {
@@ -399,8 +381,49 @@ __device__ __forceinline__ void elem_pair_hvp(const int4 c, const double* __rest
     Acc a = acc_prod(G[k].h, G[k].l, h[0].h, h[0].l);
 #pragma unroll
     for (int r = 1; r < 3; ++r) acc_fma(a, G[4 * r + k].h, G[4 * r + k].l, h[r].h, h[r].l);
-    sink_pair(gu, k, idx[k], acc_pair(a));
+    hc[k] = acc_pair(a);
   }
+}
+
+// The same in float-pair arithmetic (FP64 data); fb2 = 2 fbar as a pair.
+template <typename Sink, bool PREP = false, bool USPLIT = false>
+__device__ __forceinline__ void elem_pair_hvp(const int4 c, const double* __restrict__ Gs,
+                                              const double* __restrict__ u,
+                                              const double* __restrict__ v, Pair fb2,
+                                              const Sink& gu, bool& bad) {
+  Pair G[12];
+#pragma unroll
+  for (int i = 0; i < 12; i += 2) {
+    if constexpr (PREP) {
+      const float4 q = *reinterpret_cast<const float4*>(Gs + i);
+      G[i] = Pair{q.x, q.y};
+      G[i + 1] = Pair{q.z, q.w};
+    } else {
+      const double2 q = *reinterpret_cast<const double2*>(Gs + i);
+      G[i] = split_f64(q.x);
+      G[i + 1] = split_f64(q.y);
+    }
+  }
+  const int idx[4] = {c.x, c.y, c.z, c.w};
+  Pair U[4], V[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    if constexpr (USPLIT) {
+      const float2 qu = __ldg(reinterpret_cast<const float2*>(u) + idx[k]);
+      const float2 qv = __ldg(reinterpret_cast<const float2*>(v) + idx[k]);
+      U[k] = Pair{qu.x, qu.y};
+      V[k] = Pair{qv.x, qv.y};
+    } else {
+      const double uk = __ldg(u + idx[k]), vk = __ldg(v + idx[k]);
+      bad |= !pair_in_range(uk) || !pair_in_range(vk);
+      U[k] = split_f64(uk);
+      V[k] = split_f64(vk);
+    }
+  }
+  Pair hc[4];
+  elem_pair_hvp_core(G, U, V, fb2, hc);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) sink_pair(gu, k, idx[k], hc[k]);
 }
 
 }  // namespace kg

@@ -459,6 +459,9 @@ __global__ void __launch_bounds__(512) qf_pair_reduce_kernel(const float4* __res
   constexpr int CX = 32, PY = 16;
   __shared__ Acc red[PY][CX][2];
   __shared__ double fred[32];
+  // launched as a programmatic dependent of the fused kernel: wait until that
+  // grid has completed and its partials are visible
+  grid_dependency_wait();
   const int cx = threadIdx.x % CX, py = threadIdx.x / CX;
   const int jp = blockIdx.x * CX + cx;
   Acc s0 = acc_zero(), s1 = acc_zero();
@@ -704,11 +707,22 @@ kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const vo
   count_launch();
   if (e != cudaSuccess) return cuda_fail(e, "qf pair fused kernel");
   const int npairs = (int)(p->n / 2);
-  qf_pair_reduce_kernel<<<(npairs + 31) / 32, 512, 0, s>>>(
-      static_cast<const float4*>(p->partials), p->qf.grid, npairs, p->fpart,
-      static_cast<double*>(gx), static_cast<double*>(f), accumulate);
+  // programmatic dependent launch: the reduce kernel's launch overlaps the fused
+  // kernel's last CTAs; it waits for that grid's completion before reading
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((npairs + 31) / 32);
+  cfg.blockDim = dim3(512);
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, qf_pair_reduce_kernel, static_cast<const float4*>(p->partials),
+                         p->qf.grid, npairs, static_cast<const double*>(p->fpart),
+                         static_cast<double*>(gx), static_cast<double*>(f), accumulate);
   count_launch();
-  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "qf pair reduce kernel");
+  if (e != cudaSuccess) return cuda_fail(e, "qf pair reduce kernel");
   return KG_OK;
 }
 

@@ -173,10 +173,11 @@ static int env_choice(const char* name, const char* const* words, const int* val
 
 kg_status kg_options_apply_env(kg_options* o) {
   if (!o) return fail(KG_ERR_INVALID_ARG, "kg_options_apply_env: NULL options");
-  static const char* const sw[] = {"auto", "atomic", "csr", "transpose", "fused", "shared", "warp"};
+  static const char* const sw[] = {"auto", "atomic", "csr", "transpose", "fused", "shared", "warp",
+                                   "tile"};
   static const int sv[] = {KG_STRATEGY_AUTO, KG_STRATEGY_ATOMIC, KG_STRATEGY_CSR,
                            KG_STRATEGY_TRANSPOSE, KG_STRATEGY_FUSED, KG_STRATEGY_SHARED,
-                           KG_STRATEGY_WARP};
+                           KG_STRATEGY_WARP, KG_STRATEGY_TILE};
   static const char* const mw[] = {"auto", "recompute", "tape"};
   static const int mv[] = {KG_MODE_AUTO, KG_MODE_RECOMPUTE, KG_MODE_TAPE};
   static const char* const aw[] = {"auto", "native", "pair"};
@@ -184,7 +185,7 @@ kg_status kg_options_apply_env(kg_options* o) {
   static const char* const cw[] = {"0", "1"};
   static const int cv[] = {0, 1};
   kg_options r = *o;
-  if (env_choice("KG_STRATEGY", sw, sv, 7, &r.strategy) || env_choice("KG_MODE", mw, mv, 3, &r.mode) ||
+  if (env_choice("KG_STRATEGY", sw, sv, 8, &r.strategy) || env_choice("KG_MODE", mw, mv, 3, &r.mode) ||
       env_choice("KG_ARITH", aw, av, 3, &r.arith) || env_choice("KG_CHECK", cw, cv, 2, &r.check))
     return KG_ERR_INVALID_ARG;
   *o = r;
@@ -250,7 +251,7 @@ kg_status kg_create(kg_problem** out, int kind, const int64_t* sizes, int nsizes
   if (kg_options_apply_env(&o) != KG_OK) return KG_ERR_INVALID_ARG;
   if (o.dtype != KG_F64 && o.dtype != KG_F32)
     return fail(KG_ERR_INVALID_ARG, "kg_create: dtype must be KG_F64 or KG_F32");
-  if (o.strategy < KG_STRATEGY_AUTO || o.strategy > KG_STRATEGY_WARP)
+  if (o.strategy < KG_STRATEGY_AUTO || o.strategy > KG_STRATEGY_TILE)
     return fail(KG_ERR_INVALID_ARG, "kg_create: bad strategy");
   if (o.mode < KG_MODE_AUTO || o.mode > KG_MODE_TAPE)
     return fail(KG_ERR_INVALID_ARG, "kg_create: bad mode");

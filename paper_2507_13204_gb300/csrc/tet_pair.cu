@@ -596,6 +596,21 @@ static kg_status tet_staged_t(kg_problem* p, int mode, const void* x, void* f, v
   return e == cudaSuccess ? KG_OK : cuda_fail(e, names[mode]);
 }
 
+kg_status tet_split_vertex_values(kg_problem* p, const void* x, const void* v, void* gx, bool zero_gx,
+                                  const float2** us, const float2** vs, cudaStream_t s) {
+  float2* u2 = static_cast<float2*>(p->usplit);
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((p->n + 255) / 256, (int64_t)num_sms() * 8));
+  pair_split_vec_kernel<<<g, 256, 0, s>>>(static_cast<const double*>(x), static_cast<const double*>(v),
+                                          p->n, u2, u2 + p->n,
+                                          zero_gx ? static_cast<double*>(gx) : nullptr, p->err);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "split vertex values");
+  *us = u2;
+  *vs = v ? u2 + p->n : nullptr;
+  return KG_OK;
+}
+
 kg_status tet_staged(kg_problem* p, int mode, const void* x, void* f, void* gx, const void* seed,
                      cudaStream_t s, const void* v, bool zero_gx) {
   return p->dtype == KG_F64 ? tet_staged_t<double>(p, mode, x, f, gx, seed, v, zero_gx, s)

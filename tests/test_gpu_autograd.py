@@ -26,7 +26,7 @@ def _tet(api, mesh, dtype=torch.float64, **kw):
 
 
 @pytest.mark.parametrize("policy,mode", [("tape", "tape"), ("recompute", "recompute"), ("auto", "auto")])
-@pytest.mark.parametrize("strategy", ["atomic", "warp", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "warp", "tile", "csr"])
 def test_gradcheck_6x4cubed_mesh(mods, policy, mode, strategy):
     api, ag = mods
     mesh = W.tet_mesh(4, perm_seed=3)  # 4x4x4 cubes: 384 tets, 125 vertices

@@ -1,6 +1,6 @@
 """GPU parity: tet-mesh energy value and gradient (atomic scatter, shared-memory
-and warp aggregated scatters, CSR gather; recompute and tape) through the C ABI
-vs the CPU oracle."""
+and warp aggregated scatters, the tiled reverse pass, CSR gather; recompute and
+tape) through the C ABI vs the CPU oracle."""
 import numpy as np
 import pytest
 import torch
@@ -30,7 +30,7 @@ MESHES = [(1, None), (3, 2), (7, None), (12, 2), (25, 2)]
 
 
 @pytest.mark.parametrize("a,jit", MESHES)
-@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "tile", "csr"])
 def test_f64_grad_matches_oracle(api, a, jit, strategy):
     mesh = W.tet_mesh(a, jitter_seed=jit, perm_seed=a)
     u = np.random.default_rng(a).uniform(-1, 1, mesh.nv)
@@ -45,7 +45,7 @@ def test_f64_grad_matches_oracle(api, a, jit, strategy):
     assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
 
 
-@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "tile", "csr"])
 def test_f32_matches_oracle_on_rounded_inputs(api, strategy):
     mesh = W.tet_mesh(20, jitter_seed=2, perm_seed=3)
     u = np.random.default_rng(5).uniform(-1, 1, mesh.nv)
@@ -76,7 +76,7 @@ def test_f32_forward_ragged_counts(api, box):
     assert rel_scalar(fe.item(), O.tet_value(mesh.conn, G32, u)) <= TOL["f32"]
 
 
-@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "tile", "csr"])
 def test_tape_mode_seed_and_accumulate(api, strategy):
     mesh = W.tet_mesh(9, jitter_seed=2, perm_seed=4)
     u = np.random.default_rng(6).uniform(-1, 1, mesh.nv)
@@ -136,7 +136,7 @@ def test_full_size_100_cubed_f64(api):
     mesh, u = W.tet_inputs(100)
     f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
     ut = torch.tensor(u, device="cuda")
-    for strategy in ("atomic", "shared", "warp", "csr"):
+    for strategy in ("atomic", "shared", "warp", "tile", "csr"):
         p = _problem(api, mesh, torch.float64, strategy=strategy)
         f, g = p.grad(ut)
         fe = p.eval(ut)
@@ -172,8 +172,10 @@ def test_checked_kernels_flag_connectivity_changed_after_create(api):
 
 
 @pytest.mark.parametrize("arith", ["pair", "native"])
-@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "csr"])
+@pytest.mark.parametrize("strategy", ["atomic", "shared", "warp", "tile", "csr"])
 def test_pair_and_native_match_oracle_jittered(api, arith, strategy):
+    if strategy == "tile" and arith == "native":
+        pytest.skip("the tiled reverse pass is float-pair only (test_tile_rules)")
     mesh = W.tet_mesh(18, jitter_seed=2, perm_seed=5)
     u = np.random.default_rng(21).uniform(-1, 1, mesh.nv)
     f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u, fbar=1.3)
@@ -219,7 +221,7 @@ def test_ragged_tiles_and_tiny_meshes(api):
         u = np.random.default_rng(a * b * c).uniform(-1, 1, mesh.nv)
         f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
         for arith in ("pair", "native"):
-            for strategy in ("atomic", "shared", "warp"):
+            for strategy in ("atomic", "shared", "warp") + (("tile",) if arith == "pair" else ()):
                 p = _problem(api, mesh, torch.float64, arith=arith, strategy=strategy)
                 f, g = p.grad(torch.tensor(u, device="cuda"))
                 p.sync()
@@ -227,7 +229,7 @@ def test_ragged_tiles_and_tiny_meshes(api):
                 assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
 
 
-@pytest.mark.parametrize("strategy", ["shared", "warp"])
+@pytest.mark.parametrize("strategy", ["shared", "warp", "tile"])
 @pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
 def test_aggregation_with_scattered_element_order(api, dtype, strategy):
     # elements in random order: a 256-tet tile then touches ~1000 distinct vertices, close to
@@ -255,7 +257,57 @@ def test_strategy_defaults(api):
     conn = torch.tensor(mesh.conn, device="cuda")
     p64 = api.TetEnergy(conn, torch.tensor(mesh.G, device="cuda"), mesh.nv)
     p32 = api.TetEnergy(conn, torch.tensor(mesh.G, dtype=torch.float32, device="cuda"), mesh.nv)
-    assert p64.config[0] == "warp" and p32.config[0] == "warp"
+    assert p64.config[0] == "warp" and p32.config[0] == "tile"
+    p32c = api.TetEnergy(conn, torch.tensor(mesh.G, dtype=torch.float32, device="cuda"), mesh.nv,
+                         check=True)
+    assert p32c.config[0] == "warp"  # bounds-checked kernels: the staged kernel's warp combine
+
+
+def test_tile_rules(api):
+    # the tiled reverse pass runs for FP32 data and for FP64 data in float pairs with the
+    # prepared G, without bounds checks
+    from paper_2507_13204_gb300 import _lib as L
+    mesh = W.tet_mesh(3)
+    conn = torch.tensor(mesh.conn, device="cuda")
+    G64 = torch.tensor(mesh.G, device="cuda")
+    for kw in ({"arith": "native"}, {"check": True}, {"tape_budget_bytes": 96 * mesh.ne - 8}):
+        with pytest.raises(L.KGError) as ei:
+            api.TetEnergy(conn, G64, mesh.nv, strategy="tile", **kw)
+        assert ei.value.status == L.KG_ERR_UNSUPPORTED, kw
+    with pytest.raises(L.KGError) as ei:
+        api.TetEnergy(conn, G64.float(), mesh.nv, strategy="tile", check=True)
+    assert ei.value.status == L.KG_ERR_UNSUPPORTED
+    assert api.TetEnergy(conn, G64.float(), mesh.nv, strategy="tile").config[0] == "tile"
+
+
+@pytest.mark.parametrize("ne", [1, 31, 32, 33, 64, 65, 1537])
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+def test_tile_boundaries_and_a_vertex_shared_by_a_whole_tile(api, ne, dtype):
+    # a fan around vertex 0 (every tet has it: a tile's vertex 0 sums all 32 of its
+    # elements) with element counts around the 32-element tile and the FP32 kernel's
+    # two-tile step; the other vertices are shared by consecutive tets (a strip), in random
+    # global numbering; seed and accumulate
+    rng = np.random.default_rng(ne)
+    nv = ne + 3
+    conn = np.zeros((ne, 4), dtype=np.int32)
+    for e in range(ne):
+        conn[e] = (0, e + 1, e + 2, e + 3)
+    perm = rng.permutation(nv).astype(np.int32)
+    conn = perm[conn]
+    G = rng.uniform(-1, 1, (ne, 12))
+    u = rng.uniform(-1, 1, nv)
+    if dtype == torch.float32:
+        G, u = f32_round(G), f32_round(u)
+    f_ref, g_ref = O.tet_grad(conn, G, u, fbar=0.75)
+    p = api.TetEnergy(torch.tensor(conn, device="cuda"), torch.tensor(G, dtype=dtype, device="cuda"),
+                      nv, strategy="tile")
+    seed = torch.tensor(0.75, dtype=dtype, device="cuda")
+    g = torch.full((nv,), 1.5, dtype=dtype, device="cuda")
+    f, _ = p.grad(torch.tensor(u, dtype=dtype, device="cuda"), gx=g, seed=seed, accumulate=True)
+    p.sync()
+    tol = TOL["f64"] if dtype == torch.float64 else TOL["f32"]
+    assert rel_scalar(f.item(), f_ref) <= tol
+    assert rel_l2(g.cpu().numpy().astype(np.float64) - 1.5, g_ref) <= tol
 
 
 def test_prepared_G_and_on_the_fly_split_agree(api):
