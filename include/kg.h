@@ -86,9 +86,13 @@ typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
 
 /* Reverse-pass schedule for gathers (Sec. 3.3 and Sec. 5).
  *   ATOMIC    reuse the forward schedule; scatter-adds are atomic adds.
- *   CSR       (tet) atomic-free: per-element adjoints go to a tape, then each
- *             vertex gathers its incident entries through the transposed
- *             connectivity built at kg_create; bitwise run-to-run reproducible.
+ *   CSR       (tet) atomic-free and bitwise run-to-run reproducible: the
+ *             element adjoints of each tile of 32 consecutive elements are
+ *             summed per tile vertex in a fixed order (the tiles of
+ *             KG_STRATEGY_TILE, built at kg_create) into a partials buffer,
+ *             then each vertex adds its tiles' partials in ascending order.
+ *             FP64 problems in NATIVE arithmetic and bounds-checked problems
+ *             reach the tile sums through the tape (per-element adjoints).
  *   TRANSPOSE (dense) a second kernel reads A by columns: xbar = A^T ybar.
  *             (sparse) atomic-free: a row kernel stores y, then a team per
  *             column of the transpose (built at kg_create) gathers
@@ -235,10 +239,13 @@ kg_status kg_grad(kg_problem *p, const void *x, void *f, void *gx, void *gdata,
 kg_status kg_eval_tape(kg_problem *p, const void *x, void *f, kg_stream s);
 
 /* TAPE mode: reverse pass from the tape as the last call that wrote it left
- * it: kg_eval_tape, or (TET, CSR strategy) kg_grad, whose reverse pass goes
- * through the same tape.  kg_tape_generation tells the two apart.
+ * it: kg_eval_tape, or (TET, CSR strategy in NATIVE arithmetic or with bounds
+ * checks) kg_grad, whose reverse pass goes through the same tape.
+ * kg_tape_generation tells the two apart.
  * TET: gx[v] (+)= fbar * sum over incidences (e,k) of v of c_e[k], by atomic
- * scatter or by the CSR gather (the problem's strategy); reads no G.
+ * scatter, per-tile sums (TILE: one atomic per tile vertex; CSR: the
+ * reproducible partials and vertex gather) (the problem's strategy); reads
+ * no G.
  * LAPLACE1D: the reverse chain from y alone, ybar = 2 fbar y and
  * gx_j (+)= 3 (2 ybar_j - ybar_{j-1} - ybar_{j+1}); reads neither x nor b.
  * KG_ERR_STATE if no tape was recorded. */
@@ -246,7 +253,8 @@ kg_status kg_grad_from_tape(kg_problem *p, void *gx, const void *seed, int accum
                             kg_stream s);
 
 /* Number of launches so far that wrote the problem's tape (kg_eval_tape, and
- * kg_grad of a TET problem with the CSR strategy).  A caller that records a
+ * kg_grad of a TET problem with the CSR strategy in NATIVE arithmetic or with
+ * bounds checks).  A caller that records a
  * tape and replays it later (e.g. an autograd backward) compares the value
  * taken after its kg_eval_tape with the current one: if they differ, another
  * call overwrote the tape in between and the reverse pass must recompute.

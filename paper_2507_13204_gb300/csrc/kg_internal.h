@@ -74,8 +74,8 @@ struct kg_problem {
   void* aprep = nullptr;     // FP64 pair: A (dense) or G (tet) split into float pairs
   bool tape_valid = false;
   uint64_t tape_gen = 0;     // launches that wrote the tape (kg_tape_generation)
-  int* rowptr = nullptr;     // tet CSR: [N_v + 1]; sparse CSC: colptr [n + 1]
-  int* inc = nullptr;        // tet CSR: [4 N_e], entries (e << 2) | k; sparse CSC: row of each entry
+  int* rowptr = nullptr;     // tet CSR: [N_v + 2]; sparse CSC: colptr [n + 1]
+  int* inc = nullptr;        // tet CSR: slots (tile * 128 + j) by vertex; sparse CSC: row of each entry
   void* valT = nullptr;      // sparse CSC: values in column order
   void* usplit = nullptr;    // tet pair: u and v as float pairs [2][N_v], split per call
   // tet TILE strategy (tet_tile.cu): per tile of 32 elements, its distinct
@@ -85,6 +85,7 @@ struct kg_problem {
   uint8_t* tile_vptr = nullptr;
   uint8_t* tile_inc = nullptr;
   int ntiles = 0;
+  void* tile_part = nullptr;  // tet CSR strategy: the tile vertex sums [tile][128]
   void* xdev = nullptr;      // kg_grad_host staging
   void* gdev = nullptr;
   void* fdev = nullptr;
@@ -155,11 +156,22 @@ kg_status tet_tile_run(kg_problem* p, int mode, const float2* us, const float2* 
                        const void* seed, cudaStream_t s);
 kg_status tet_tile_run_f32(kg_problem* p, int mode, const void* x, const void* v, void* f, void* gx,
                            const void* seed, cudaStream_t s);
+// reproducible CSR strategy on the tiles: set-up (tiles, partials, vertex ->
+// slot buckets; synchronises s) and the vertex gather of the tile partials
+kg_status tet_tile_csr_setup(kg_problem* p, cudaStream_t s);
+kg_status tet_tile_gather(kg_problem* p, void* gx, int accumulate, cudaStream_t s);
+// reverse pass from the tape over the tiles (CSR: partials then gather; TILE:
+// one reduction per tile vertex)
+kg_status tet_tile_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate, cudaStream_t s);
 // u (and v) of a float-pair tet problem split into float pairs in the
 // problem's workspace, gx zeroed when zero_gx (tet_pair.cu); *us / *vs receive
 // the pairs
 kg_status tet_split_vertex_values(kg_problem* p, const void* x, const void* v, void* gx, bool zero_gx,
                                   const float2** us, const float2** vs, cudaStream_t s);
+
+// In-place exclusive scan of data[0..n) into data[0..n] (data[n] = total; one
+// CTA, set-up only; tet.cu).
+void scan_exclusive(int* data, int n, cudaStream_t s);
 
 // Buckets of positions by key (transposed index lists; tet.cu), synchronises s.
 kg_status build_buckets(const int* keys, int64_t count, int nbins, int* binptr, int* perm,

@@ -7,8 +7,8 @@
 // is c_e = G_e^T (2 fbar g_e / (1 + |g_e|^2)), and each gathered read becomes
 // the scatter-add gu[conn[e][k]] += c_e[k] -- atomic when the reverse reuses
 // the forward schedule (KG_STRATEGY_ATOMIC, the paper's choice), or an
-// atomic-free gather over the transposed connectivity (KG_STRATEGY_CSR: the
-// rescheduling proposed in Sec. 5).  In TAPE mode the forward stores c_e (for
+// atomic-free, reproducible reverse over per-tile transposed connectivity
+// (KG_STRATEGY_CSR, tet_tile.cu: the rescheduling proposed in Sec. 5).  In TAPE mode the forward stores c_e (for
 // fbar = 1) so that the reverse pass reads neither G nor u (Sec. 5, taping
 // allocated once outside the kernel).
 //
@@ -181,24 +181,6 @@ __global__ void __launch_bounds__(256) tet_direct_f32_kernel(DirectArgs a) {
   finish_sum<float>(block_sum((double)fa + (double)fc, red), a.fpart, a.counter, a.f, 0, red);
 }
 
-// Atomic-free reverse: thread per vertex gathers its incidences, in ascending
-// (e, k) order, from the tape: gu[v] (+)= fbar * sum_p tape[inc[p]].
-template <typename T>
-__global__ void __launch_bounds__(256) tet_csr_gather_kernel(const int* __restrict__ rowptr,
-                                                             const int* __restrict__ inc,
-                                                             const T* __restrict__ tape, int nv,
-                                                             const T* seed, T* gu, int accumulate) {
-  const T fb = load_seed(seed);
-  const int stride = gridDim.x * blockDim.x;
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
-    const int p0 = rowptr[v], p1 = rowptr[v + 1];
-    T s = T(0);
-    for (int p = p0; p < p1; ++p) s += tape[inc[p]];
-    const T r = fb * s;
-    gu[v] = accumulate ? gu[v] + r : r;
-  }
-}
-
 // ------------------------------------------------- set-up kernels ---------
 __global__ void tet_validate_kernel(const int* __restrict__ conn, int64_t n4, int nv,
                                     unsigned* err) {
@@ -328,7 +310,8 @@ kg_status tet_setup(kg_problem* p, cudaStream_t s) {
     return fail(KG_ERR_UNSUPPORTED, "TETENERGY TILE strategy: needs FP64 data in PAIR arithmetic "
                                     "with the prepared G (within tape_budget_bytes) and check = 0");
   if (p->mode == KG_MODE_AUTO) p->mode = tape_bytes <= budget ? KG_MODE_TAPE : KG_MODE_RECOMPUTE;
-  if (p->mode == KG_MODE_TAPE || p->strategy == KG_STRATEGY_CSR) {
+  // the CSR strategy goes through the tape where no tile kernel computes the elements
+  if (p->mode == KG_MODE_TAPE || (p->strategy == KG_STRATEGY_CSR && !tet_tile_supported(p))) {
     if ((rc = ws_alloc(p, &p->tape, tape_bytes, "tape c_e")) != KG_OK) return rc;
   }
   if ((rc = tet_staged_setup(p)) != KG_OK) return rc;
@@ -346,15 +329,11 @@ kg_status tet_setup(kg_problem* p, cudaStream_t s) {
     if (h & ERRBIT_BOUNDS) return fail(KG_ERR_BOUNDS, "kg_create: connectivity entry outside [0, N_v)");
   }
   if (p->strategy == KG_STRATEGY_TILE) return tet_tile_setup(p, s);
-  if (p->strategy == KG_STRATEGY_CSR) {
-    if ((rc = ws_alloc(p, (void**)&p->rowptr, sizeof(int) * (size_t)(p->n + 1), "CSR rowptr")) != KG_OK)
-      return rc;
-    if ((rc = ws_alloc(p, (void**)&p->inc, sizeof(int) * (size_t)n4, "CSR incidences")) != KG_OK)
-      return rc;
-    if ((rc = build_buckets(conn, n4, (int)p->n, p->rowptr, p->inc, s)) != KG_OK) return rc;
-  }
+  if (p->strategy == KG_STRATEGY_CSR) return tet_tile_csr_setup(p, s);
   return KG_OK;
 }
+
+void scan_exclusive(int* data, int n, cudaStream_t s) { csr_scan_kernel<<<1, 1024, 0, s>>>(data, n); }
 
 // Buckets of the positions of keys[0..count) by key value (keys in [0, nbins)):
 // binptr[k] .. binptr[k+1] delimit, in perm, the positions i with keys[i] == k,
@@ -458,13 +437,8 @@ template <typename T>
 static kg_status tet_scatter_t(kg_problem* p, void* gx, const void* seed, int accumulate,
                                cudaStream_t s) {
   cudaError_t e;
-  if (p->strategy == KG_STRATEGY_CSR) {
-    prof_begin(s, "tet_csr_gather_kernel");
-    tet_csr_gather_kernel<T><<<grid_for(p->n, 256, 8), 256, 0, s>>>(
-        p->rowptr, p->inc, static_cast<const T*>(p->tape), (int)p->n, static_cast<const T*>(seed),
-        static_cast<T*>(gx), accumulate);
-    prof_end(s);
-    count_launch();
+  if (p->strategy == KG_STRATEGY_CSR || p->strategy == KG_STRATEGY_TILE) {
+    return tet_tile_from_tape(p, gx, seed, accumulate, s);
   } else {
     if (!accumulate) {
       if ((e = cudaMemsetAsync(gx, 0, sizeof(T) * (size_t)p->n, s)) != cudaSuccess)
@@ -490,9 +464,21 @@ template <typename T>
 static kg_status tet_grad_t(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
                             int accumulate, cudaStream_t s) {
   if (p->strategy == KG_STRATEGY_CSR) {
-    kg_status rc = tet_eval(p, x, f, true, s);
-    if (rc != KG_OK) return rc;
-    return tet_scatter_t<T>(p, gx, seed, accumulate, s);
+    // reproducible: tile partials in fixed order, then the vertex gather in fixed order;
+    // through the tape where no tile kernel computes the elements
+    kg_status rc;
+    if (!tet_tile_supported(p)) {
+      if ((rc = tet_eval(p, x, f, true, s)) != KG_OK) return rc;
+      return tet_tile_from_tape(p, gx, seed, accumulate, s);
+    }
+    if (sizeof(T) == 4) {
+      rc = tet_tile_run_f32(p, TS_GRAD, x, nullptr, f, gx, seed, s);
+    } else {
+      const float2 *us = nullptr, *vs = nullptr;
+      if ((rc = tet_split_vertex_values(p, x, nullptr, gx, false, &us, &vs, s)) != KG_OK) return rc;
+      rc = tet_tile_run(p, TS_GRAD, us, nullptr, f, gx, seed, s);
+    }
+    return rc == KG_OK ? tet_tile_gather(p, gx, accumulate, s) : rc;
   }
   // pair arithmetic: the kernel that splits u also zeroes gu (one launch for both)
   const bool fold_zero = p->arith == KG_ARITH_PAIR && sizeof(T) == 8;
@@ -529,6 +515,17 @@ kg_status tet_grad(kg_problem* p, const void* x, void* f, void* gx, const void* 
 kg_status tet_hvp(kg_problem* p, const void* x, const void* v, void* hv, const void* seed,
                   int accumulate, cudaStream_t s) {
   const bool fold_zero = p->arith == KG_ARITH_PAIR && p->dtype == KG_F64;
+  if (p->strategy == KG_STRATEGY_CSR && tet_tile_supported(p)) {  // reproducible, as the gradient
+    kg_status rc;
+    if (p->dtype == KG_F32) {
+      rc = tet_tile_run_f32(p, TS_HVP, x, v, nullptr, hv, seed, s);
+    } else {
+      const float2 *us = nullptr, *vs = nullptr;
+      if ((rc = tet_split_vertex_values(p, x, v, hv, false, &us, &vs, s)) != KG_OK) return rc;
+      rc = tet_tile_run(p, TS_HVP, us, vs, nullptr, hv, seed, s);
+    }
+    return rc == KG_OK ? tet_tile_gather(p, hv, accumulate, s) : rc;
+  }
   if (p->strategy == KG_STRATEGY_TILE) {
     if (p->dtype == KG_F32) {
       if (!accumulate) {

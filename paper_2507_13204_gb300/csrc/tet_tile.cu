@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <string>
+#include <type_traits>
 
 #include "kg_device.cuh"
 #include "kg_internal.h"
@@ -146,6 +147,7 @@ struct TileArgs {
   const uint8_t* inc;
   const double* seed;
   double* gu;
+  float2* part;             // STORE: the tile vertex sums (float pairs), [tile][TL_C]
   double* fpart;
   unsigned* counter;
   double* f;
@@ -159,8 +161,9 @@ struct TileArgs {
 // memory) with the tiled scatter: a warp's 32 elements are one tile; their
 // adjoints go to the warp's slice of shared memory, and after a __syncwarp
 // lane j takes tile vertices j, j + 32, ...: it adds the vertex's incidences
-// in ascending order and issues one global reduction.
-template <int MODE>
+// in ascending order and issues one global reduction -- or, STORE (the
+// reproducible CSR strategy), writes the sum to the tile's partials instead.
+template <int MODE, bool STORE>
 __global__ void __launch_bounds__(TL_THREADS, 4) tet_tile_pair_kernel(TileArgs a) {
   __shared__ float4 tab[kLogTableSize];
   __shared__ __align__(16) float2 c_s[TL_THREADS / 32][TL_C];  // float4 stores
@@ -216,7 +219,11 @@ __global__ void __launch_bounds__(TL_THREADS, 4) tet_tile_pair_kernel(TileArgs a
           s = acc_add(s, Acc{cv.x, cv.y});
         }
       }
-      if (lane < V) red_add(a.gu + vg, pair_to_double_fast(acc_pair(s)));
+      if (lane < V) {
+        const Pair pr = acc_pair(s);
+        if constexpr (STORE) a.part[t * TL_C + lane] = make_float2(pr.h, pr.l);
+        else red_add(a.gu + vg, pair_to_double_fast(pr));
+      }
     }
     for (int j = lane + 32; j < V; j += 32) {  // tiles of more than 32 distinct vertices
       const int q0 = __ldg(vp + j), q1 = __ldg(vp + j + 1);
@@ -225,7 +232,9 @@ __global__ void __launch_bounds__(TL_THREADS, 4) tet_tile_pair_kernel(TileArgs a
         const float2 cv = cw[__ldg(ic + q)];
         s = acc_add(s, Acc{cv.x, cv.y});
       }
-      red_add(a.gu + __ldg(a.vlist + t * TL_C + j), pair_to_double_fast(acc_pair(s)));
+      const Pair pr = acc_pair(s);
+      if constexpr (STORE) a.part[t * TL_C + j] = make_float2(pr.h, pr.l);
+      else red_add(a.gu + __ldg(a.vlist + t * TL_C + j), pair_to_double_fast(pr));
     }
     __syncwarp();
   }
@@ -260,12 +269,13 @@ struct TileArgs32 {
   const uint8_t* inc;
   const float* seed;
   float* gu;
+  float* part;      // STORE: the tile vertex sums, [tile][TL_C]
   double* fpart;
   unsigned* counter;
   float* f;
 };
 
-template <int MODE>
+template <int MODE, bool STORE>
 __global__ void __launch_bounds__(TL_THREADS) tet_tile_f32_kernel(TileArgs32 a) {
   __shared__ __align__(16) float c_s[TL_THREADS / 32][2][TL_C];  // float4 stores
   __shared__ double red[32];
@@ -357,18 +367,158 @@ __global__ void __launch_bounds__(TL_THREADS) tet_tile_f32_kernel(TileArgs32 a) 
         const unsigned w = __shfl_sync(0xffffffffu, incw[h], (q >> 2) & 31);
         if (q < p1[h]) sum += c_s[warp][h][(w >> (8 * (q & 3))) & 0xFFu];
       }
-      if (lane < V[h]) red_add(a.gu + vg[h], sum);
       const int64_t t = base / TL_E + h;
+      if (lane < V[h]) {
+        if constexpr (STORE) a.part[t * TL_C + lane] = sum;
+        else red_add(a.gu + vg[h], sum);
+      }
       for (int j = lane + 32; j < V[h]; j += 32) {  // tiles of more than 32 distinct vertices
         const int q0 = __ldg(a.vptr + t * TL_VPTR + j), q1 = __ldg(a.vptr + t * TL_VPTR + j + 1);
         float s2 = 0.f;
         for (int q = q0; q < q1; ++q) s2 += c_s[warp][h][__ldg(a.inc + t * TL_C + q)];
-        red_add(a.gu + __ldg(a.vlist + t * TL_C + j), s2);
+        if constexpr (STORE) a.part[t * TL_C + j] = s2;
+        else red_add(a.gu + __ldg(a.vlist + t * TL_C + j), s2);
       }
     }
     __syncwarp();
   }
   if constexpr (!HVP) finish_sum<float>(block_sum((double)fa + (double)fc, red), a.fpart, a.counter, a.f, 0, red);
+}
+
+// ------------------------------------------------------ from the tape ----
+// The reverse pass from the tape c_e (N_e x 4 values, written by the taping
+// forward): a tile's 128 tape entries are contiguous, so each warp reads its
+// tile's with coalesced loads into shared memory and sums, per tile vertex,
+// the incidences in ascending order; the sum times fbar is stored to the
+// tile's partials (STORE) or added to gu with one reduction.  VT: 0 FP32
+// values, 1 FP64 tape summed in float pairs (FP64 problems in PAIR
+// arithmetic), 2 FP64 tape summed in FP64.
+template <int VT> struct TileVal;
+template <> struct TileVal<0> { using tape_t = float; using part_t = float; };
+template <> struct TileVal<1> { using tape_t = double; using part_t = float2; };
+template <> struct TileVal<2> { using tape_t = double; using part_t = double; };
+
+template <int VT, bool STORE>
+__global__ void __launch_bounds__(TL_THREADS) tet_tile_tape_kernel(
+    const typename TileVal<VT>::tape_t* __restrict__ tape, int ntiles, const int* __restrict__ tile_nv,
+    const int* __restrict__ vlist, const uint8_t* __restrict__ vptr, const uint8_t* __restrict__ inc,
+    const typename TileVal<VT>::tape_t* seed, typename TileVal<VT>::tape_t* gu,
+    typename TileVal<VT>::part_t* part) {
+  using T = typename TileVal<VT>::tape_t;
+  using S = std::conditional_t<VT == 1, Acc, T>;
+  __shared__ __align__(16) S c_s[TL_THREADS / 32][TL_C];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const T fb = load_seed(seed);
+  const Pair fbp = split_f64((double)fb);
+  S* cw = c_s[warp];
+  const int nwarps = gridDim.x * (TL_THREADS / 32);
+  for (int t = blockIdx.x * (TL_THREADS / 32) + warp; t < ntiles; t += nwarps) {
+    const int V = __ldg(tile_nv + t);
+    const int n4 = V ? __ldg(vptr + (int64_t)t * TL_VPTR + V) : 0;  // 4 n_t
+    const unsigned incw = __ldg(reinterpret_cast<const unsigned*>(inc + (int64_t)t * TL_C) + lane);
+    const int p0 = lane < V ? __ldg(vptr + (int64_t)t * TL_VPTR + lane) : 0;
+    const int p1 = lane < V ? __ldg(vptr + (int64_t)t * TL_VPTR + lane + 1) : 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int q = 4 * lane + k;
+      if (q < n4) {
+        const T c = __ldcs(tape + (int64_t)t * TL_C + q);
+        if constexpr (VT == 1) {
+          const Pair pc = split_f64(c);
+          cw[q] = Acc{pc.h, pc.l};
+        } else {
+          cw[q] = c;
+        }
+      }
+    }
+    __syncwarp();
+    const int rounds = (int)__reduce_max_sync(0xffffffffu, (unsigned)(p1 - p0));
+    S sum{};
+    for (int r = 0; r < rounds; ++r) {
+      const int q = p0 + r;
+      const unsigned w = __shfl_sync(0xffffffffu, incw, (q >> 2) & 31);
+      if (q < p1) {
+        const S cv = cw[(w >> (8 * (q & 3))) & 0xFFu];
+        if constexpr (VT == 1) sum = acc_add(sum, cv);
+        else sum += cv;
+      }
+    }
+    auto finish = [&](int j, S sv) {
+      if constexpr (VT == 1) {
+        const Pair pr = pair_mul(acc_pair(sv), fbp);
+        if constexpr (STORE) part[(int64_t)t * TL_C + j] = make_float2(pr.h, pr.l);
+        else red_add(gu + __ldg(vlist + (int64_t)t * TL_C + j), pair_to_double_fast(pr));
+      } else {
+        if constexpr (STORE) part[(int64_t)t * TL_C + j] = fb * sv;
+        else red_add(gu + __ldg(vlist + (int64_t)t * TL_C + j), fb * sv);
+      }
+    };
+    if (lane < V) finish(lane, sum);
+    for (int j = lane + 32; j < V; j += 32) {  // tiles of more than 32 distinct vertices
+      const int q0 = __ldg(vptr + (int64_t)t * TL_VPTR + j), q1 = __ldg(vptr + (int64_t)t * TL_VPTR + j + 1);
+      S s2{};
+      for (int q = q0; q < q1; ++q) {
+        const S cv = cw[__ldg(inc + (int64_t)t * TL_C + q)];
+        if constexpr (VT == 1) s2 = acc_add(s2, cv);
+        else s2 += cv;
+      }
+      finish(j, s2);
+    }
+    __syncwarp();
+  }
+}
+
+// Second pass of the reproducible CSR strategy: vertex v adds the partials of
+// its tiles in ascending tile order, perm[rowptr[v] .. rowptr[v+1]) listing
+// the slots (tile * TL_C + local vertex) of v (built at kg_create).
+template <int VT>
+__global__ void __launch_bounds__(256) tet_tile_gather_kernel(const int* __restrict__ rowptr,
+                                                              const int* __restrict__ perm,
+                                                              const typename TileVal<VT>::part_t* __restrict__ part,
+                                                              int nv, typename TileVal<VT>::tape_t* gu,
+                                                              int accumulate) {
+  using T = typename TileVal<VT>::tape_t;
+  const int stride = gridDim.x * blockDim.x;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += stride) {
+    const int q0 = __ldg(rowptr + v), q1 = __ldg(rowptr + v + 1);
+    T r;
+    if constexpr (VT == 1) {
+      Acc s = acc_zero();
+      for (int q = q0; q < q1; ++q) {
+        const float2 c = __ldg(part + __ldg(perm + q));
+        s = acc_add(s, Acc{c.x, c.y});
+      }
+      r = pair_to_double(acc_pair(s));
+    } else {
+      T s = T(0);
+      for (int q = q0; q < q1; ++q) s += __ldg(part + __ldg(perm + q));
+      r = s;
+    }
+    gu[v] = accumulate ? gu[v] + r : r;
+  }
+}
+
+// The valid tile slots (tile t, local vertex j < V_t), compacted: slot
+// toff[t] + j gets key vlist[t][j] (its vertex) and id t * TL_C + j.  toff is
+// the exclusive scan of tile_nv.
+__global__ void tile_slot_compact_kernel(const int* __restrict__ tile_nv, const int* __restrict__ toff,
+                                         const int* __restrict__ vlist, int ntiles, int* keys, int* ids) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)ntiles * TL_C; i += stride) {
+    const int t = (int)(i / TL_C), j = (int)(i % TL_C);
+    if (j < __ldg(tile_nv + t)) {
+      const int c = __ldg(toff + t) + j;
+      keys[c] = __ldg(vlist + i);
+      ids[c] = (int)i;
+    }
+  }
+}
+
+// perm[q] <- ids[perm[q]]: bucket positions (compact slots, ascending) to slot ids
+// (also ascending, as the compaction keeps the slot order).
+__global__ void tile_slot_ids_kernel(const int* __restrict__ ids, int n, int* perm) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += stride) perm[q] = __ldg(ids + perm[q]);
 }
 
 // ---------------------------------------------------------------- host ----
@@ -394,9 +544,9 @@ kg_status tet_tile_setup(kg_problem* p, cudaStream_t s) {
   return e == cudaSuccess ? KG_OK : cuda_fail(e, "tile build");
 }
 
-template <int MODE>
+template <int MODE, bool STORE>
 static cudaError_t launch_tile(const kg_problem* p, const TileArgs& a, cudaStream_t s) {
-  auto kern = tet_tile_pair_kernel<MODE>;
+  auto kern = tet_tile_pair_kernel<MODE, STORE>;
   static int occ = 0;
   if (occ < 1) {
     int o = 0;
@@ -432,17 +582,21 @@ kg_status tet_tile_run(kg_problem* p, int mode, const float2* us, const float2* 
   a.K = log_consts();
   kg_status rc = logtab_for_device(&a.logtab);
   if (rc != KG_OK) return rc;
-  const char* name = mode == TS_HVP ? "tet_tile_pair_kernel<hvp>" : "tet_tile_pair_kernel<grad>";
+  const bool store = p->strategy == KG_STRATEGY_CSR;
+  a.part = static_cast<float2*>(p->tile_part);
+  const char* name = mode == TS_HVP ? (store ? "tet_tile_pair_kernel<hvp, partials>" : "tet_tile_pair_kernel<hvp>")
+                                    : (store ? "tet_tile_pair_kernel<grad, partials>" : "tet_tile_pair_kernel<grad>");
   prof_begin(s, name);
-  cudaError_t e = mode == TS_HVP ? launch_tile<TS_HVP>(p, a, s) : launch_tile<TS_GRAD>(p, a, s);
+  cudaError_t e = mode == TS_HVP ? (store ? launch_tile<TS_HVP, true>(p, a, s) : launch_tile<TS_HVP, false>(p, a, s))
+                                 : (store ? launch_tile<TS_GRAD, true>(p, a, s) : launch_tile<TS_GRAD, false>(p, a, s));
   prof_end(s);
   count_launch();
   return e == cudaSuccess ? KG_OK : cuda_fail(e, name);
 }
 
-template <int MODE>
+template <int MODE, bool STORE>
 static cudaError_t launch_tile32(const kg_problem* p, const TileArgs32& a, cudaStream_t s) {
-  auto kern = tet_tile_f32_kernel<MODE>;
+  auto kern = tet_tile_f32_kernel<MODE, STORE>;
   static int occ = 0;
   if (occ < 1) {
     int o = 0;
@@ -473,12 +627,131 @@ kg_status tet_tile_run_f32(kg_problem* p, int mode, const void* x, const void* v
   a.fpart = p->fpart;
   a.counter = p->counter;
   a.f = static_cast<float*>(f);
-  const char* name = mode == TS_HVP ? "tet_tile_f32_kernel<hvp>" : "tet_tile_f32_kernel<grad>";
+  const bool store = p->strategy == KG_STRATEGY_CSR;
+  a.part = static_cast<float*>(p->tile_part);
+  const char* name = mode == TS_HVP ? (store ? "tet_tile_f32_kernel<hvp, partials>" : "tet_tile_f32_kernel<hvp>")
+                                    : (store ? "tet_tile_f32_kernel<grad, partials>" : "tet_tile_f32_kernel<grad>");
   prof_begin(s, name);
-  cudaError_t e = mode == TS_HVP ? launch_tile32<TS_HVP>(p, a, s) : launch_tile32<TS_GRAD>(p, a, s);
+  cudaError_t e = mode == TS_HVP ? (store ? launch_tile32<TS_HVP, true>(p, a, s) : launch_tile32<TS_HVP, false>(p, a, s))
+                                 : (store ? launch_tile32<TS_GRAD, true>(p, a, s) : launch_tile32<TS_GRAD, false>(p, a, s));
   prof_end(s);
   count_launch();
   return e == cudaSuccess ? KG_OK : cuda_fail(e, name);
+}
+
+// Value type of the tile partials / tape sums of this problem.
+static int tile_vt(const kg_problem* p) {
+  return p->dtype == KG_F32 ? 0 : p->arith == KG_ARITH_PAIR ? 1 : 2;
+}
+
+// The reproducible CSR strategy's set-up: the tiles, the partials buffer and
+// the vertex -> slot buckets (ascending slots per vertex), over the valid
+// slots only.  Synchronises s.
+kg_status tet_tile_csr_setup(kg_problem* p, cudaStream_t s) {
+  kg_status rc = tet_tile_setup(p, s);
+  if (rc != KG_OK) return rc;
+  const int64_t nslots = (int64_t)p->ntiles * TL_C;
+  if (nslots >= (int64_t(1) << 31)) return fail(KG_ERR_INVALID_ARG, "TETENERGY CSR: too many tiles");
+  const size_t vsz = tile_vt(p) == 0 ? sizeof(float) : tile_vt(p) == 1 ? sizeof(float2) : sizeof(double);
+  if ((rc = ws_alloc(p, &p->tile_part, vsz * (size_t)nslots, "tile partials")) != KG_OK ||
+      (rc = ws_alloc(p, (void**)&p->rowptr, sizeof(int) * (size_t)(p->n + 1), "vertex -> slot pointers")) != KG_OK)
+    return rc;
+  // exclusive scan of the tiles' vertex counts: the compact slot offsets
+  int* toff = nullptr;
+  if (dev_alloc((void**)&toff, sizeof(int) * ((size_t)p->ntiles + 1)) != cudaSuccess)
+    return fail(KG_ERR_OOM, "tile offsets allocation failed");
+  cudaError_t e = cudaMemcpyAsync(toff, p->tile_nv, sizeof(int) * (size_t)p->ntiles, cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess) {
+    scan_exclusive(toff, p->ntiles, s);
+    e = cudaGetLastError();
+  }
+  int nvalid = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&nvalid, toff + p->ntiles, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    cudaFree(toff);
+    return cuda_fail(e, "tile slot offsets");
+  }
+  int *keys = nullptr, *ids = nullptr;
+  rc = ws_alloc(p, (void**)&p->inc, sizeof(int) * (size_t)std::max(nvalid, 1), "vertex -> slot lists");
+  if (rc == KG_OK && (dev_alloc((void**)&keys, sizeof(int) * (size_t)std::max(nvalid, 1)) != cudaSuccess ||
+                      dev_alloc((void**)&ids, sizeof(int) * (size_t)std::max(nvalid, 1)) != cudaSuccess))
+    rc = fail(KG_ERR_OOM, "tile slot keys allocation failed");
+  if (rc == KG_OK) {
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nslots + 255) / 256, (int64_t)num_sms() * 8));
+    tile_slot_compact_kernel<<<g, 256, 0, s>>>(p->tile_nv, toff, p->tile_vlist, p->ntiles, keys, ids);
+    e = cudaGetLastError();
+    rc = e == cudaSuccess ? build_buckets(keys, nvalid, (int)p->n, p->rowptr, p->inc, s)
+                          : cuda_fail(e, "tile slot compaction");
+  }
+  if (rc == KG_OK && nvalid > 0) {
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((nvalid + 255) / 256, (int64_t)num_sms() * 8));
+    tile_slot_ids_kernel<<<g, 256, 0, s>>>(ids, nvalid, p->inc);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "tile slot ids");
+  }
+  cudaFree(keys);
+  cudaFree(ids);
+  cudaFree(toff);
+  return rc;
+}
+
+// Second pass of the CSR strategy: gx[v] (+)= the sum of v's tile partials.
+kg_status tet_tile_gather(kg_problem* p, void* gx, int accumulate, cudaStream_t s) {
+  const int g = (int)std::max<int64_t>(1, std::min<int64_t>((p->n + 255) / 256, (int64_t)num_sms() * 8));
+  // a second-stage sum like the dense partials reduction: not bracketed by the profiling events
+  switch (tile_vt(p)) {
+    case 0:
+      tet_tile_gather_kernel<0><<<g, 256, 0, s>>>(p->rowptr, p->inc, static_cast<const float*>(p->tile_part),
+                                                  (int)p->n, static_cast<float*>(gx), accumulate);
+      break;
+    case 1:
+      tet_tile_gather_kernel<1><<<g, 256, 0, s>>>(p->rowptr, p->inc, static_cast<const float2*>(p->tile_part),
+                                                  (int)p->n, static_cast<double*>(gx), accumulate);
+      break;
+    default:
+      tet_tile_gather_kernel<2><<<g, 256, 0, s>>>(p->rowptr, p->inc, static_cast<const double*>(p->tile_part),
+                                                  (int)p->n, static_cast<double*>(gx), accumulate);
+  }
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? KG_OK : cuda_fail(e, "tile gather");
+}
+
+template <int VT, bool STORE>
+static void launch_tape_pass(const kg_problem* p, const void* seed, void* gx, cudaStream_t s) {
+  using T = typename TileVal<VT>::tape_t;
+  using PT = typename TileVal<VT>::part_t;
+  const int64_t g = std::max<int64_t>(1, std::min<int64_t>(((int64_t)p->ntiles + 7) / 8, (int64_t)num_sms() * 8));
+  tet_tile_tape_kernel<VT, STORE><<<(int)g, TL_THREADS, 0, s>>>(
+      static_cast<const T*>(p->tape), p->ntiles, p->tile_nv, p->tile_vlist, p->tile_vptr, p->tile_inc,
+      static_cast<const T*>(seed), static_cast<T*>(gx), static_cast<PT*>(p->tile_part));
+}
+
+// The reverse pass from the tape: CSR strategy, the tile partials then the
+// vertex gather (reproducible); TILE strategy, one reduction per tile vertex
+// into gx (zeroed here unless accumulating).
+kg_status tet_tile_from_tape(kg_problem* p, void* gx, const void* seed, int accumulate, cudaStream_t s) {
+  const bool store = p->strategy == KG_STRATEGY_CSR;
+  cudaError_t e;
+  if (!store && !accumulate) {
+    if ((e = cudaMemsetAsync(gx, 0, p->esize * (size_t)p->n, s)) != cudaSuccess) return cuda_fail(e, "zero gu");
+    count_launch();
+  }
+  prof_begin(s, store ? "tet_tile_tape_kernel<partials>" : "tet_tile_tape_kernel");
+  switch (tile_vt(p) * 2 + (store ? 1 : 0)) {
+    case 0: launch_tape_pass<0, false>(p, seed, gx, s); break;
+    case 1: launch_tape_pass<0, true>(p, seed, gx, s); break;
+    case 2: launch_tape_pass<1, false>(p, seed, gx, s); break;
+    case 3: launch_tape_pass<1, true>(p, seed, gx, s); break;
+    case 4: launch_tape_pass<2, false>(p, seed, gx, s); break;
+    default: launch_tape_pass<2, true>(p, seed, gx, s); break;
+  }
+  prof_end(s);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "tile tape pass");
+  return store ? tet_tile_gather(p, gx, accumulate, s) : KG_OK;
 }
 
 }  // namespace kg

@@ -312,8 +312,10 @@ def test_tile_boundaries_and_a_vertex_shared_by_a_whole_tile(api, ne, dtype):
 
 def test_prepared_G_and_on_the_fly_split_agree(api):
     # FP64 pair arithmetic keeps G split into float pairs when 96 N_e bytes fit the workspace
-    # budget; below it the kernels split G on every call.  Same split, same results (the CSR
-    # gather and the fixed-order value sum are bitwise reproducible).
+    # budget; below it the kernels split G on every call.  With the CSR strategy the prepared
+    # G runs the tile kernel (partials in float pairs), the on-the-fly split goes through the
+    # tape (FP64 adjoints summed as pairs): the same sums in another rounding, each bitwise
+    # reproducible run to run.
     mesh = W.tet_mesh(10, jitter_seed=3, perm_seed=6)
     u = np.random.default_rng(8).uniform(-1, 1, mesh.nv)
     f_ref, g_ref = O.tet_grad(mesh.conn, mesh.G, u)
@@ -329,9 +331,14 @@ def test_prepared_G_and_on_the_fly_split_agree(api):
         p.sync()
         assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
         assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+        f2, g2 = p.grad(ut)
+        p.sync()
+        assert torch.equal(f, f2) and torch.equal(g, g2)
         out.append((f.clone(), g.clone(), fe.clone()))
-    for a, b in zip(*out):
-        assert torch.equal(a, b)
+    (fp, gp, ep), (ff, gf, ef) = out
+    assert torch.equal(ep, ef)  # the forward is one kernel for both
+    assert rel_scalar(fp.item(), ff.item()) <= 1e-13
+    assert rel_l2(gp.cpu().numpy(), gf.cpu().numpy()) <= 1e-13
 
 
 def test_warp_combine_on_a_mesh_where_every_tet_shares_one_vertex(api):
