@@ -807,14 +807,16 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
 # fingerprint it was taken with; after any change to them the field is null until re-measured.
 _CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_13204_gb300", "csrc")
 _TRAFFIC = {
-    ("dense", "f64"): (812285952, ["quadform_pair.cu", "kg_pair.cuh", "kg_device.cuh"],
-                       "d0bc63f67f82d63e"),
-    ("dense32", "f32"): (403951104, ["quadform_f32.cu", "kg_pair.cuh", "kg_device.cuh"],
-                         "a2f7a0d457fa7b5a"),
-    ("tet", "f64"): (708342528, ["tet_pair.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
-                     "c062cc9df2927b68"),
-    ("tet32", "f32"): (394994176, ["tet.cu", "kg_tet_elem.cuh", "kg_pair.cuh", "kg_device.cuh"],
-                       "dddf18082dcb690f"),
+    ('dense', 'f64'): (815457536, ['quadform_pair.cu', 'kg_pair.cuh', 'kg_device.cuh'],
+                        '9cb7f542ed5dd002'),
+    ('dense32', 'f32'): (406857984, ['quadform_f32.cu', 'kg_pair.cuh', 'kg_device.cuh'],
+                          '7a908754a44fcb95'),
+    ('tet', 'f64'): (711262976, ['tet_pair.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                      '912296069bea1346'),
+    ('tet32', 'f32'): (469311232, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                        '81897ebbcc4c3357'),
+    ('tetcsr', 'f64'): (787844864, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                         '81897ebbcc4c3357'),
 }
 
 

@@ -351,8 +351,9 @@ kg_status kg_check_bounded_wait(kg_problem *p, uint64_t limit_ns, kg_stream s);
 /* Rates of this GPU that set the ALU rooflines of the native-FP64 kernels
  * (and motivate the float-pair arithmetic), measured by small kernels of the
  * library: eight independent register FMA chains per thread over 4 CTAs of
- * 256 threads per SM (FP64, FP32), and red.global.add to pseudo-random slots
- * of an 8 MiB array (FP64, FP32).  Best of three timed launches each, after a
+ * 256 threads per SM (FP64, FP32; FP64 log1p and division in the same
+ * pattern), and red.global.add to pseudo-random slots of an 8 MiB array
+ * (FP64, FP32).  Best of three timed launches each, after a
  * warm-up.  Allocates and frees an 8 MiB scratch array and synchronises `s`
  * (a characterisation call, not a per-call entry point).  No passage: device
  * characterisation for the roofline. */
@@ -361,6 +362,8 @@ typedef struct {
   double fp32_fma_tflops; /* FP32 FMA rate, 1e12 flop/s */
   double fp64_red_gops;   /* FP64 red.global.add to random L2-resident slots, 1e9/s */
   double fp32_red_gops;   /* FP32 red.global.add, same pattern, 1e9/s */
+  double fp64_log1p_gops; /* FP64 log1p (CUDA's), eight dependent chains a thread, 1e9/s */
+  double fp64_div_gops;   /* FP64 division, the same pattern, 1e9/s */
   int sms;                /* streaming multiprocessors */
   int l2_bytes;           /* L2 cache size */
 } kg_box_rates;

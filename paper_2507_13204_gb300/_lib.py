@@ -43,6 +43,7 @@ class kg_options(ctypes.Structure):
 class kg_box_rates(ctypes.Structure):
     _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
                 ("fp64_red_gops", ctypes.c_double), ("fp32_red_gops", ctypes.c_double),
+                ("fp64_log1p_gops", ctypes.c_double), ("fp64_div_gops", ctypes.c_double),
                 ("sms", ctypes.c_int), ("l2_bytes", ctypes.c_int)]
 
 

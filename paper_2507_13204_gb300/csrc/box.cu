@@ -4,6 +4,7 @@
 //   - FP64 and FP32 FMA rates: every thread runs eight independent FMA chains
 //     in registers (enough independent work per warp scheduler to keep either
 //     pipe busy), over a few waves of CTAs on every SM;
+//   - FP64 log1p and division rates, in the same chained pattern;
 //   - FP64 and FP32 reduction rates: every thread issues red.global.add to
 //     pseudo-random slots (xorshift) of an 8 MiB array, the scatter-add pattern
 //     of the tet and sparse gradients at an L2-resident footprint.
@@ -36,6 +37,37 @@ __global__ void __launch_bounds__(kBoxBlock) fma_rate_kernel(T* sink, int iters,
 #pragma unroll
   for (int c = 0; c < kChains; ++c) s += v[c];
   if (s == (T)-1234.5) sink[0] = s;  // never true for these inputs
+}
+
+// FP64 log1p and division: eight independent chains per thread, each step
+// feeding the previous result back (log1p of a value in [0, 2); a / b with b
+// in [1, 2)), so that neither is hoisted out of the loop.
+__global__ void __launch_bounds__(kBoxBlock) log1p_rate_kernel(double* sink, int iters) {
+  double v[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) v[c] = 0.5 + 1e-3 * (threadIdx.x + c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) v[c] = log1p(v[c] + 1.0);
+  }
+  double s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += v[c];
+  if (s == -1234.5) sink[0] = s;
+}
+
+__global__ void __launch_bounds__(kBoxBlock) div_rate_kernel(double* sink, int iters, double b) {
+  double v[kChains];
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) v[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) v[c] = (v[c] + 1.0) / b;
+  }
+  double s = 0;
+#pragma unroll
+  for (int c = 0; c < kChains; ++c) s += v[c];
+  if (s == -1234.5) sink[0] = s;
 }
 
 template <typename T>
@@ -115,6 +147,15 @@ extern "C" kg_status kg_measure_box(kg_box_rates* out, kg_stream stream) {
     rc = time_best([&] { red_rate_kernel<float><<<rgrid, kBoxBlock, 0, s>>>(
                              static_cast<float*>(buf), kSlots - 1, per); }, s, &ms);
   if (rc == KG_OK) out->fp32_red_gops = reds / (ms * 1e-3) / 1e9;
+  const int itl = 64;
+  if (rc == KG_OK)
+    rc = time_best([&] { log1p_rate_kernel<<<grid, kBoxBlock, 0, s>>>(static_cast<double*>(buf), itl); }, s,
+                   &ms);
+  if (rc == KG_OK) out->fp64_log1p_gops = threads * itl * kChains / (ms * 1e-3) / 1e9;
+  if (rc == KG_OK)
+    rc = time_best([&] { div_rate_kernel<<<grid, kBoxBlock, 0, s>>>(static_cast<double*>(buf), itl, 1.25); }, s,
+                   &ms);
+  if (rc == KG_OK) out->fp64_div_gops = threads * itl * kChains / (ms * 1e-3) / 1e9;
   out->sms = sms;
   out->l2_bytes = l2;
   cudaStreamSynchronize(s);
