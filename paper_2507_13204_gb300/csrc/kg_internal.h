@@ -39,6 +39,7 @@ struct QfConfig {
   int grid = 1;     // CTAs
   int rows_per_cta = 1;
   int streamed = 0;  // 1: FP32 TMA-streamed kernel (quadform_f32.cu)
+  int coop = 0;      // 1: the float-pair gradient reduces its partials in one cooperative launch
 };
 
 struct kg_problem_impl;
@@ -122,6 +123,9 @@ kg_status qf_pair_prepare(kg_problem* p, cudaStream_t s);
 // dst[i] = float pair (h, l) of src[i] for i < count (count even, 16-byte aligned)
 kg_status pair_prepare(const double* src, void* dst, int64_t count, cudaStream_t s);
 int qf_pair_grid(const kg_problem* p, int* band);
+// Whether the warp-specialized pair gradient can run as one cooperative launch
+// (its whole grid resident at once); the test hook KG_TEST_NO_COOP=1 says no.
+bool qf_pair_coop_fits(const kg_problem* p);
 kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
                        int accumulate, cudaStream_t s);

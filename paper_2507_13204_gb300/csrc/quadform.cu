@@ -354,8 +354,9 @@ kg_status qf_setup(kg_problem* p, cudaStream_t s) {
     c.grid = qf_pair_grid(p, &c.rows_per_cta);
     c.team = c.block = 512;
     kg_status rc = ws_alloc(p, &p->partials, 8 * (size_t)c.grid * p->n, "xbar partials (pairs)");
-    if (rc != KG_OK) return rc;
-    return qf_pair_prepare(p, s);
+    if (rc == KG_OK) rc = qf_pair_prepare(p, s);
+    if (rc == KG_OK) c.coop = qf_pair_coop_fits(p) ? 1 : 0;
+    return rc;
   }
   if (p->arith == KG_ARITH_AUTO || p->dtype == KG_F32) p->arith = KG_ARITH_NATIVE;
   if (qf_f32_supported(p)) {  // FP32: rows streamed through shared memory by TMA

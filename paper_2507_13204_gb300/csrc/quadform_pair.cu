@@ -26,6 +26,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <string>
 
 #include "kg_device.cuh"
@@ -49,8 +50,10 @@ struct QpArgs {
   float4* partials;  // [grid][n/2] of (h0, l0, h1, l1)
   double* fpart;
   unsigned* counter;
-  double* f;  // EVAL: written by the last CTA
+  double* f;  // EVAL: written by the last CTA; fused reduction: by CTA 0
   unsigned* err;
+  double* gx;      // fused reduction (qf_pair_ws_kernel<KP, true>): the gradient
+  int accumulate;  // fused reduction: 1 adds to gx
 };
 
 __device__ __forceinline__ Acc shfl_xor_acc(Acc a, int o) {
@@ -270,7 +273,117 @@ constexpr int WS_DW = 7, WS_UW = 8;             // dot and update warps
 constexpr int WS_THREADS = (WS_DW + WS_UW + 1) * 32;
 constexpr int WS_SLOTS = 5;
 
-template <int KP>
+// Fixed-order sum of the per-CTA float-pair partials over column pairs
+// [j0, j1), by a CTA of 512 threads: thread (cx, py), py < 15, adds partials
+// py, py + 15, ... of column pair cx of each block of 34 (twelve loads in
+// flight); the 15 sums are added in py order and converted to double once per
+// column.  Threads 510 and 511 only join the barriers.  The order depends on
+// neither the CTA nor the range, so the fused kernel's tail and the separate
+// reduce kernel give the same bits.
+constexpr int RED_CX = 34, RED_PY = 15, RED_LOADS = 12;
+
+__device__ __forceinline__ void reduce_pair_columns(const float4* partials, int nparts, int npairs,
+                                                    int j0, int j1, double* gx, int accumulate,
+                                                    Acc (*red)[RED_CX][2]) {
+  const int cx = threadIdx.x % RED_CX, py = threadIdx.x / RED_CX;
+  for (int jb = j0; jb < j1; jb += RED_CX) {
+    const int jp = jb + cx;
+    Acc s0 = acc_zero(), s1 = acc_zero();
+    if (py < RED_PY && jp < j1) {
+      for (int c = py; c < nparts; c += RED_LOADS * RED_PY) {
+        float4 v[RED_LOADS];
+#pragma unroll
+        for (int u = 0; u < RED_LOADS; ++u)
+          if (c + RED_PY * u < nparts) v[u] = __ldcg(partials + (int64_t)(c + RED_PY * u) * npairs + jp);
+#pragma unroll
+        for (int u = 0; u < RED_LOADS; ++u)
+          if (c + RED_PY * u < nparts) {
+            s0 = acc_add(s0, Acc{v[u].x, v[u].y});
+            s1 = acc_add(s1, Acc{v[u].z, v[u].w});
+          }
+      }
+    }
+    if (py < RED_PY) {
+      red[py][cx][0] = s0;
+      red[py][cx][1] = s1;
+    }
+    __syncthreads();
+    if (py == 0 && jp < j1) {
+      Acc t0 = red[0][cx][0], t1 = red[0][cx][1];
+#pragma unroll
+      for (int g = 1; g < RED_PY; ++g) {
+        t0 = acc_add(t0, red[g][cx][0]);
+        t1 = acc_add(t1, red[g][cx][1]);
+      }
+      const double g0 = pair_to_double(acc_pair(t0)), g1 = pair_to_double(acc_pair(t1));
+      double2* o = reinterpret_cast<double2*>(gx) + jp;
+      if (accumulate) {
+        const double2 old = *o;
+        *o = make_double2(old.x + g0, old.y + g1);
+      } else {
+        *o = make_double2(g0, g1);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// The f partials' sum, by all threads of a CTA (the same order in both paths).
+__device__ __forceinline__ void reduce_f_partials(const double* fpart, int nparts, double* f, double* scratch) {
+  double fs = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) fs += __ldcg(fpart + i);
+  fs = block_sum(fs, scratch);
+  if (threadIdx.x == 0) *f = fs;
+}
+
+// The partials' reduction as the tail of the fused kernel (a cooperative
+// launch: every CTA is resident).  Each CTA counts itself in (a.counter[2])
+// once its partials and f partial are written and waits, bounded, until all
+// have.  With more than one CTA, CTA 0 sums the f partials while CTAs 1 ..
+// grid - 1 sum their shares of the column pairs, [(b - 1) npairs / (grid - 1),
+// b npairs / (grid - 1)) (at most 34 pairs, one block, for n <= 10336 on 152
+// CTAs); a single CTA does both.  The last CTA to count itself out
+// (a.counter[3]) resets both counters for the next launch.
+__device__ __forceinline__ void ws_grid_reduce(const QpArgs& a, int npairs) {
+  static_assert(WS_THREADS == 512, "reduce_pair_columns takes 512 threads");
+  __shared__ Acc red[RED_PY][RED_CX][2];
+  __shared__ double fred[32];
+  __shared__ int go;
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's partials (ordered before by the barrier) first
+    atomicAdd(a.counter + 2, 1u);
+    bool ok = true;
+    const uint64_t t0 = global_ns();
+    while (ld_acquire_u32(a.counter + 2) < gridDim.x) {
+      if (global_ns() - t0 > kWaitLimitNs) {
+        set_error(a.err, ERRBIT_TIMEOUT);
+        ok = false;
+        break;
+      }
+    }
+    __threadfence();
+    go = ok;
+  }
+  __syncthreads();
+  if (go) {
+    const int nparts = gridDim.x;
+    const int cols = nparts > 1 ? nparts - 1 : 1, b = nparts > 1 ? (int)blockIdx.x - 1 : 0;
+    if (b >= 0) {
+      const int j0 = (int)((int64_t)b * npairs / cols), j1 = (int)((int64_t)(b + 1) * npairs / cols);
+      reduce_pair_columns(a.partials, nparts, npairs, j0, j1, a.gx, a.accumulate, red);
+    }
+    if (blockIdx.x == 0 && a.f) reduce_f_partials(a.fpart, nparts, a.f, fred);
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.counter + 3, 1u) == gridDim.x - 1) {
+      a.counter[2] = 0u;
+      a.counter[3] = 0u;
+    }
+  }
+}
+
+template <int KP, bool GRIDRED>
 __global__ void __launch_bounds__(WS_THREADS, 1) qf_pair_ws_kernel(QpArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   constexpr int H = 128 * KP;                       // column pairs of a chunk slot
@@ -447,71 +560,23 @@ __global__ void __launch_bounds__(WS_THREADS, 1) qf_pair_ws_kernel(QpArgs a) {
   }
   __syncwarp();
   __syncthreads();
+  if constexpr (GRIDRED) ws_grid_reduce(a, npairs);
 }
 
-// Fixed-order sum of the per-CTA float-pair partials: thread (cx, py) adds
-// partials py, py+16, ... of column pair cx; the 16 sums are then added in py
-// order and converted to double once per column.  Block 0 also writes f.
+// The same reduction as a separate kernel: block b sums column pairs
+// [34 b, 34 b + 34); block 0 also writes f.
 __global__ void __launch_bounds__(512) qf_pair_reduce_kernel(const float4* __restrict__ partials,
                                                              int nparts, int npairs,
                                                              const double* __restrict__ fpart,
                                                              double* gx, double* f, int accumulate) {
-  constexpr int CX = 32, PY = 16;
-  __shared__ Acc red[PY][CX][2];
+  __shared__ Acc red[RED_PY][RED_CX][2];
   __shared__ double fred[32];
   // launched as a programmatic dependent of the fused kernel: wait until that
   // grid has completed and its partials are visible
   grid_dependency_wait();
-  const int cx = threadIdx.x % CX, py = threadIdx.x / CX;
-  const int jp = blockIdx.x * CX + cx;
-  Acc s0 = acc_zero(), s1 = acc_zero();
-  if (jp < npairs) {
-    int c = py;
-    for (; c + 3 * PY < nparts; c += 4 * PY) {  // four independent loads in flight
-      const float4 v0 = __ldcs(partials + (int64_t)c * npairs + jp);
-      const float4 v1 = __ldcs(partials + (int64_t)(c + PY) * npairs + jp);
-      const float4 v2 = __ldcs(partials + (int64_t)(c + 2 * PY) * npairs + jp);
-      const float4 v3 = __ldcs(partials + (int64_t)(c + 3 * PY) * npairs + jp);
-      s0 = acc_add(s0, Acc{v0.x, v0.y});
-      s1 = acc_add(s1, Acc{v0.z, v0.w});
-      s0 = acc_add(s0, Acc{v1.x, v1.y});
-      s1 = acc_add(s1, Acc{v1.z, v1.w});
-      s0 = acc_add(s0, Acc{v2.x, v2.y});
-      s1 = acc_add(s1, Acc{v2.z, v2.w});
-      s0 = acc_add(s0, Acc{v3.x, v3.y});
-      s1 = acc_add(s1, Acc{v3.z, v3.w});
-    }
-    for (; c < nparts; c += PY) {
-      const float4 v = __ldcs(partials + (int64_t)c * npairs + jp);
-      s0 = acc_add(s0, Acc{v.x, v.y});
-      s1 = acc_add(s1, Acc{v.z, v.w});
-    }
-  }
-  red[py][cx][0] = s0;
-  red[py][cx][1] = s1;
-  __syncthreads();
-  if (py == 0 && jp < npairs) {
-    Acc t0 = red[0][cx][0], t1 = red[0][cx][1];
-#pragma unroll
-    for (int i = 1; i < PY; ++i) {
-      t0 = acc_add(t0, red[i][cx][0]);
-      t1 = acc_add(t1, red[i][cx][1]);
-    }
-    const double g0 = pair_to_double(acc_pair(t0)), g1 = pair_to_double(acc_pair(t1));
-    double2* o = reinterpret_cast<double2*>(gx) + jp;
-    if (accumulate) {
-      const double2 old = *o;
-      *o = make_double2(old.x + g0, old.y + g1);
-    } else {
-      *o = make_double2(g0, g1);
-    }
-  }
-  if (blockIdx.x == 0 && f) {
-    double fs = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) fs += fpart[i];
-    fs = block_sum(fs, fred);
-    if (threadIdx.x == 0) *f = fs;
-  }
+  const int j0 = blockIdx.x * RED_CX;
+  reduce_pair_columns(partials, nparts, npairs, j0, min(j0 + RED_CX, npairs), gx, accumulate, red);
+  if (blockIdx.x == 0 && f) reduce_f_partials(fpart, nparts, f, fred);
 }
 
 // The prepared copy of A: every double split into its float pair (h, l).
@@ -672,24 +737,71 @@ static size_t ws_smem(int kp) {
   return (size_t)WS_SLOTS * 128 * kp * 16 + (2 * WS_SLOTS + 2) * 8 + 16 * sizeof(Acc) + 16;
 }
 
+// fused: the partials' reduction runs in the kernel's tail (ws_grid_reduce),
+// which needs every CTA resident at once: a cooperative launch, which the
+// runtime refuses when the grid does not fit.
 template <int KP>
-static cudaError_t launch_ws(int grid, cudaStream_t s, const QpArgs& a) {
-  auto kern = qf_pair_ws_kernel<KP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)ws_smem(KP));
-  if (e != cudaSuccess) return e;
-  kern<<<grid, WS_THREADS, ws_smem(KP), s>>>(a);
+static cudaError_t launch_ws(int grid, cudaStream_t s, const QpArgs& a, bool fused) {
+  const size_t smem = ws_smem(KP);
+  cudaError_t e;
+  if (fused) {
+    auto kern = qf_pair_ws_kernel<KP, true>;
+    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+      return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(WS_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, a);
+  }
+  auto kern = qf_pair_ws_kernel<KP, false>;
+  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return e;
+  kern<<<grid, WS_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
-static cudaError_t dispatch_ws(int kp, int grid, cudaStream_t s, const QpArgs& a) {
+static cudaError_t dispatch_ws(int kp, int grid, cudaStream_t s, const QpArgs& a, bool fused) {
   switch (kp) {
-    case 8: return launch_ws<8>(grid, s, a);
-    case 12: return launch_ws<12>(grid, s, a);
-    case 16: return launch_ws<16>(grid, s, a);
-    case 20: return launch_ws<20>(grid, s, a);
+    case 8: return launch_ws<8>(grid, s, a, fused);
+    case 12: return launch_ws<12>(grid, s, a, fused);
+    case 16: return launch_ws<16>(grid, s, a, fused);
+    case 20: return launch_ws<20>(grid, s, a, fused);
   }
   return cudaErrorInvalidValue;
+}
+
+template <int KP>
+static bool ws_coop_fits(int grid) {
+  int dev = 0, coop = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+    return false;
+  auto kern = qf_pair_ws_kernel<KP, true>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem(KP)) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WS_THREADS, ws_smem(KP)) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return (int64_t)per_sm * num_sms() >= grid;
+}
+
+bool qf_pair_coop_fits(const kg_problem* p) {
+  if (const char* env = std::getenv("KG_TEST_NO_COOP"))
+    if (std::atoi(env) == 1) return false;
+  switch (ws_kp(p)) {
+    case 8: return ws_coop_fits<8>(p->qf.grid);
+    case 12: return ws_coop_fits<12>(p->qf.grid);
+    case 16: return ws_coop_fits<16>(p->qf.grid);
+    case 20: return ws_coop_fits<20>(p->qf.grid);
+  }
+  return false;
 }
 
 kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
@@ -698,11 +810,28 @@ kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const vo
     return fail(KG_ERR_INVALID_ARG, "QUADFORM pair kernels need 16-byte aligned x and gx");
   QpArgs a = pair_args(p, x, seed);
   const int kp = ws_kp(p);
+  cudaError_t e;
+  if (kp && p->qf.coop) {
+    // one launch: the partials' reduction in the kernel's tail
+    a.gx = static_cast<double*>(gx);
+    a.f = static_cast<double*>(f);
+    a.accumulate = accumulate;
+    prof_begin(s, "qf_pair_ws_kernel<fused, prepared A, grid reduction>");
+    e = dispatch_ws(kp, p->qf.grid, s, a, true);
+    prof_end(s);
+    count_launch();
+    if (e == cudaSuccess) return KG_OK;
+    if (e != cudaErrorCooperativeLaunchTooLarge) return cuda_fail(e, "qf pair fused kernel");
+    cudaGetLastError();  // the grid is not resident at once here: two launches from now on
+    p->qf.coop = 0;
+    a.gx = nullptr;
+    a.f = nullptr;
+  }
   prof_begin(s, kp ? "qf_pair_ws_kernel<fused, prepared A>"
                   : p->aprep ? "qf_pair_kernel<fused, prepared A>" : "qf_pair_kernel<fused>");
-  cudaError_t e = kp ? dispatch_ws(kp, p->qf.grid, s, a)
-                     : dispatch_pair<true>(p->aprep != nullptr, pair_ppt(p->n), p->qf.grid,
-                                           pair_smem((int)p->n), s, a);
+  e = kp ? dispatch_ws(kp, p->qf.grid, s, a, false)
+         : dispatch_pair<true>(p->aprep != nullptr, pair_ppt(p->n), p->qf.grid,
+                               pair_smem((int)p->n), s, a);
   prof_end(s);
   count_launch();
   if (e != cudaSuccess) return cuda_fail(e, "qf pair fused kernel");
@@ -710,7 +839,7 @@ kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const vo
   // programmatic dependent launch: the reduce kernel's launch overlaps the fused
   // kernel's last CTAs; it waits for that grid's completion before reading
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((npairs + 31) / 32);
+  cfg.gridDim = dim3((npairs + RED_CX - 1) / RED_CX);
   cfg.blockDim = dim3(512);
   cfg.stream = s;
   cudaLaunchAttribute at[1];

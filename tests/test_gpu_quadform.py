@@ -213,11 +213,12 @@ def test_pair_exact_cases(api):
 @pytest.mark.parametrize("m,n", [(1, 2050), (77, 4098), (200, 6146), (151, 8194), (500, 10240),
                                  (3000, 4098), (2600, 10000)])
 def test_warp_specialized_fused_kernel_shapes(api, m, n):
-    # 2048 < n <= 10240 on the prepared A runs the warp-specialized fused kernel in 2-CTA
-    # clusters: every chunk width (2..5 column pairs per role thread and chunk), odd pair
-    # counts (the two CTAs' column halves differ by one pair), a single row, ragged row
-    # counts per cluster, bands of more than 16 and 32 rows (the partial buffer and the
-    # chunk ring wrap around); a seed, and the same result on a second call
+    # 2048 < n <= 10240 on the prepared A runs the warp-specialized fused kernel: every
+    # chunk width (8..20 column pairs per update thread), odd pair counts (the second
+    # chunk of a row is shorter than the first), a single row, ragged bands, bands of more
+    # than 5 and 32 rows (the chunk ring and the two-row partial buffer wrap around), more
+    # CTAs than column-pair blocks of the in-kernel reduction and fewer; a seed, and the
+    # same result on a second call
     A, x = W.quadform_inputs(n, m=m, seed=m + n)
     f_ref, g_ref = O.quadform_grad(A, x, fbar=0.5)
     p = api.QuadForm(torch.tensor(A, device="cuda"))
@@ -232,3 +233,34 @@ def test_warp_specialized_fused_kernel_shapes(api, m, n):
     assert rel_l2(g1.cpu().numpy(), g_ref) <= TOL["f64"]
     assert torch.equal(f, f1) and torch.equal(g, g1)
     p.close()
+
+
+@pytest.mark.parametrize("m,n", [(1, 2050), (151, 8194), (2600, 10000)])
+def test_one_launch_and_two_launch_reductions_agree_bitwise(api, m, n, monkeypatch):
+    # the partials' reduction in the fused kernel's tail (one cooperative launch) and the
+    # separate reduce kernel (two launches; KG_TEST_NO_COOP=1 at create) add the same
+    # partials in the same order: same bits, also when accumulating into gx
+    from paper_2507_13204_gb300 import _lib as L
+    A, x = W.quadform_inputs(n, m=m, seed=3 * m + n)
+    f_ref, g_ref = O.quadform_grad(A, x, fbar=-1.5)
+    At, xt = torch.tensor(A, device="cuda"), torch.tensor(x, device="cuda")
+    seed = torch.tensor(-1.5, dtype=torch.float64, device="cuda")
+    out = {}
+    for coop in (1, 0):
+        if coop:
+            monkeypatch.delenv("KG_TEST_NO_COOP", raising=False)
+        else:
+            monkeypatch.setenv("KG_TEST_NO_COOP", "1")
+        p = api.QuadForm(At)
+        f, g = p.grad(xt, seed=seed)
+        launches = L.kg_last_launch_count()
+        g2 = torch.full_like(g, 0.25)
+        p.grad(xt, gx=g2, seed=seed, accumulate=True)
+        p.sync()
+        out[coop] = (f.item(), g.cpu().numpy(), g2.cpu().numpy(), launches)
+        p.close()
+    (f1, g1, a1, l1), (f0, g0, a0, l0) = out[1], out[0]
+    assert (l1, l0) == (1, 2)
+    assert rel_scalar(f1, f_ref) <= TOL["f64"] and rel_l2(g1, g_ref) <= TOL["f64"]
+    assert f1 == f0 and np.array_equal(g1, g0) and np.array_equal(a1, a0)
+    assert np.array_equal(a1, 0.25 + g1)
