@@ -611,7 +611,9 @@ class BatchedWL(Workload):
             self.xs[i].copy_(x)
         for j, (mesh, u, _, _) in enumerate(self.tets):
             self.xs[self.ndense + j].copy_(torch.tensor(u, device=dev))
-        self.batch = api.Batch(probs, arith=self.arith, strategy=self.strategy)
+        # float-pair copies of every dense A without one (the n < 1024 instances, 4.2 GB)
+        self.batch = api.Batch(probs, arith=self.arith, strategy=self.strategy, budget_bytes=8 << 30)
+        self.bound = self.batch.bind(self.xs, self.fs, self.gxs)  # pointer tables built once
         self.x_pin = self.xbuf.cpu().pin_memory()
         self.g_pin = torch.empty_like(self.gbuf, device="cpu").pin_memory()
         self.f_pin = torch.empty_like(self.fbuf, device="cpu").pin_memory()
@@ -623,15 +625,15 @@ class BatchedWL(Workload):
         self.eval_bytes = self.grad_bytes
 
     def step(self):
-        self.batch.grad(self.xs, self.fs, self.gxs)
+        self.batch.grad(self.bound)
 
     def eval_step(self):  # the per-instance launch loop (the comparison)
-        self.batch.grad_loop(self.xs, self.fs, self.gxs)
+        self.batch.grad_loop(self.bound)
 
     def e2e_step(self):
         import torch
         self.xbuf.copy_(self.x_pin, non_blocking=True)
-        self.batch.grad(self.xs, self.fs, self.gxs)
+        self.batch.grad(self.bound)
         self.g_pin.copy_(self.gbuf, non_blocking=True)
         self.f_pin.copy_(self.fbuf, non_blocking=True)
         torch.cuda.current_stream().synchronize()
@@ -653,7 +655,8 @@ class BatchedWL(Workload):
     def config(self):
         return {"workload": f"batched: {self.ndense} dense ||A_k x_k||^2 (n_k log-uniform "
                             f"[32, 2048]) + {self.ntet} tet meshes (1e3..1e5 tets), FP64, all "
-                            f"value+grads in one persistent launch (CUDA graph)",
+                            f"value+grads in one persistent launch (CUDA graph); float-pair "
+                            f"copies of the data made at create",
                 "l2": f"inputs larger than L2 ({self.grad_bytes / 1e9:.1f} GB)",
                 "comparison": "ms_eval / grad_over_eval_ratio here are the per-instance launch loop"}
 

@@ -289,6 +289,12 @@ kg_status kg_grad_host(kg_problem *p, const void *x_host, void *f_host, void *gx
  * opt->strategy picks the tet scatter: AUTO or ATOMIC (one atomic per
  * contribution) or WARP (warp-combined atomics, see KG_STRATEGY_WARP); others
  * are KG_ERR_UNSUPPORTED.
+ * FP64 batches in PAIR arithmetic stream float-pair copies of the data: the
+ * instances' own (kg_create's), and for dense instances that have none (n <
+ * 1024) one the batch makes at create, largest first, within
+ * opt->tape_budget_bytes (0 = 1 GiB); the others split their FP64 data on
+ * every load.  Like kg_create's, these copies are taken once: A must not
+ * change while the batch lives.
  * The problems are borrowed and must outlive the batch. */
 kg_status kg_batch_create(kg_batch **out, kg_problem *const *probs, int count,
                           const kg_options *opt, kg_stream s);

@@ -208,6 +208,9 @@ def kg_grad_host(h, x_host, f_host, gx_host, stream=None):
 
 
 def _table(items):
+    """ctypes array of the items' addresses (an array passes through as is)."""
+    if isinstance(items, ctypes.Array):
+        return items
     return (ctypes.c_void_p * len(items))(*[ptr(t) for t in items])
 
 

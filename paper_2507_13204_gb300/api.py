@@ -241,13 +241,24 @@ class Laplace1D(Problem):
         return self.n
 
 
+class BatchBuffers:
+    """The x, f and gx buffers of one batch call with their device-pointer tables
+    (Batch.bind).  Holds the tensors, so the addresses stay valid."""
+
+    def __init__(self, xs, fs, gxs):
+        self.xs, self.fs, self.gxs = list(xs), list(fs), list(gxs)
+        self.tables = (L._table(self.xs), L._table(self.fs), L._table(self.gxs))
+
+
 class Batch:
     """Many problems differentiated by one persistent launch (graph-replayed)."""
 
-    def __init__(self, problems, arith="auto", strategy="auto", stream=None):
+    def __init__(self, problems, arith="auto", strategy="auto", budget_bytes=0, stream=None):
+        """budget_bytes: cap on the float-pair copies of dense A that the batch makes
+        (kg_options.tape_budget_bytes; 0 = 1 GiB)."""
         self.problems = list(problems)
         opt = L.options(dtype=_DT[self.problems[0].dtype], arith=ARITHS[arith],
-                        strategy=STRATEGIES[strategy])
+                        strategy=STRATEGIES[strategy], tape_budget_bytes=int(budget_bytes))
         self.handle = L.kg_batch_create([p.handle for p in self.problems], opt, stream)
 
     @property
@@ -272,13 +283,30 @@ class Batch:
             p._vec(gxs[i], f"gxs[{i}]")
             p._one(fs[i], f"fs[{i}]")
 
-    def grad(self, xs, fs, gxs, stream=None):
-        self._check(xs, fs, gxs)
-        L.kg_grad_batched(self.handle, xs, fs, gxs, stream)
+    def bind(self, xs, fs, gxs):
+        """One set of buffers, checked in full and with its pointer tables built once.
+        Building the tables costs about a microsecond a tensor of host time: for a batch
+        of thousands of instances, milliseconds a call, as long as the batch's kernel.
+        Pass the result to grad() / grad_loop() in place of (xs, fs, gxs)."""
+        self.check_buffers(xs, fs, gxs)
+        return BatchBuffers(xs, fs, gxs)
 
-    def grad_loop(self, xs, fs, gxs, stream=None):
+    def _tables(self, xs, fs, gxs):
+        if isinstance(xs, BatchBuffers):
+            if fs is not None or gxs is not None:
+                raise ValueError("kg: pass either a BatchBuffers or (xs, fs, gxs)")
+            if len(xs.xs) != len(self.problems):
+                raise ValueError(f"kg: the batch has {len(self.problems)} problems; the bound "
+                                 f"buffers {len(xs.xs)}")
+            return xs.tables
         self._check(xs, fs, gxs)
-        L.kg_grad_batched_loop(self.handle, xs, fs, gxs, stream)
+        return L._table(xs), L._table(fs), L._table(gxs)
+
+    def grad(self, xs, fs=None, gxs=None, stream=None):
+        L.kg_grad_batched(self.handle, *self._tables(xs, fs, gxs), stream)
+
+    def grad_loop(self, xs, fs=None, gxs=None, stream=None):
+        L.kg_grad_batched_loop(self.handle, *self._tables(xs, fs, gxs), stream)
 
     def sync(self):
         L.kg_batch_sync(self.handle)

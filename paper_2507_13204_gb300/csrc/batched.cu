@@ -598,8 +598,10 @@ struct Tuning {
 int default_rows(int n) { return n <= 64 ? 128 : n <= 256 ? 64 : (n <= 1024 ? 16 : 8); }
 int default_elems(int64_t) { return 4096; }
 
-Plan make_plan(const std::vector<kg_problem*>& probs, const std::vector<int>& ids, const Tuning& tu,
-               bool pair, size_t es) {
+// prep[i]: the float-pair copy of problem i's A (dense) or G (tet) that the
+// batch streams, or NULL (the FP64 data, split per load).
+Plan make_plan(const std::vector<kg_problem*>& probs, const std::vector<const void*>& prep,
+               const std::vector<int>& ids, const Tuning& tu, bool pair, size_t es) {
   Plan P;
   struct Cost {
     double c;
@@ -614,10 +616,10 @@ Plan make_plan(const std::vector<kg_problem*>& probs, const std::vector<int>& id
     I.m = p->m;
     I.d0 = p->data0;
     I.d1 = p->data1;
-    if (pair && p->aprep && p->arith == KG_ARITH_PAIR) {  // stream the prepared float pairs
+    if (pair && prep[ids[idx]]) {  // stream the prepared float pairs
       I.prep = 1;
-      if (p->kind == KG_QUADFORM) I.d0 = p->aprep;
-      else I.d1 = p->aprep;
+      if (p->kind == KG_QUADFORM) I.d0 = prep[ids[idx]];
+      else I.d1 = prep[ids[idx]];
     }
     int64_t per;
     if (I.kind == BK_DENSE) {
@@ -762,6 +764,8 @@ kg_status launch_plan(const DevPlan& D, int dtype, bool pair, bool warp, unsigne
 
 struct kg_batch {
   std::vector<kg_problem*> probs;
+  std::vector<const void*> prep;  // per problem: the float-pair copy streamed, or NULL
+  std::vector<void*> own_preps;   // the copies the batch made itself
   int dtype = KG_F64;
   bool pair = false;
   bool warp = false;  // tet scatter: warp-combined atomics (false: one atomic per contribution)
@@ -795,7 +799,7 @@ std::string gpu_name() {
 // Times the persistent kernel on the instances `ids` with tuning `tu`.
 kg_status time_plan(kg_batch* b, const std::vector<int>& ids, const Tuning& tu, cudaStream_t s,
                     void* xbuf, void* gbuf, float* ms) {
-  Plan P = make_plan(b->probs, ids, tu, b->pair, b->es);
+  Plan P = make_plan(b->probs, b->prep, ids, tu, b->pair, b->es);
   DevPlan D;
   kg_status rc = devplan_alloc(D, P, s);
   if (rc == KG_OK) {
@@ -843,7 +847,8 @@ kg_status autotune(kg_batch* b, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   std::map<std::string, int> cache = cache_read();
   bool dirty = false;
-  const std::string prefix = b->gpu + "|" + (b->dtype == KG_F64 ? "f64" : "f32") + "|" +
+  // "k2": dense tiles of pair batches stream float-pair copies where the budget allows
+  const std::string prefix = b->gpu + "|k2|" + (b->dtype == KG_F64 ? "f64" : "f32") + "|" +
                              (b->pair ? "pair" : "native") + "|";
   // scratch x / gx for the timing runs (zeros are valid inputs for both kinds)
   size_t need = 0;
@@ -899,6 +904,7 @@ void batch_free(kg_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->dev.release();
+  for (void* q : b->own_preps) cudaFree(q);
   if (b->err) cudaFree(b->err);
   delete b;
 }
@@ -956,6 +962,36 @@ kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count,
       rc = fail(KG_ERR_UNSUPPORTED, "kg_batch_create: some data is outside the pair range");
     b->pair = pair;
   }
+  // the float-pair copies: the instances' own, else (dense instances whose
+  // kg_create took none, n < 1024) one the batch makes, largest first, within
+  // opt->tape_budget_bytes (0: 1 GiB)
+  b->prep.assign(count, nullptr);
+  if (rc == KG_OK && b->pair) {
+    size_t budget = opt && opt->tape_budget_bytes ? opt->tape_budget_bytes : (size_t(1) << 30);
+    std::vector<int> order;
+    for (int i = 0; i < count; ++i) {
+      kg_problem* p = b->probs[i];
+      if (p->aprep && p->arith == KG_ARITH_PAIR) b->prep[i] = p->aprep;
+      else if (p->kind == KG_QUADFORM) order.push_back(i);
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+      return b->probs[a]->m * b->probs[a]->n > b->probs[c]->m * b->probs[c]->n;
+    });
+    for (int i : order) {
+      kg_problem* p = b->probs[i];
+      const size_t bytes = 8 * (size_t)p->m * (size_t)p->n;
+      if (bytes > budget) continue;
+      void* q = nullptr;
+      if (dev_alloc(&q, bytes) != cudaSuccess) {
+        rc = fail(KG_ERR_OOM, "kg_batch_create: float-pair copy of A");
+        break;
+      }
+      b->own_preps.push_back(q);
+      if ((rc = pair_prepare(static_cast<const double*>(p->data0), q, p->m * p->n, s)) != KG_OK) break;
+      b->prep[i] = q;
+      budget -= bytes;
+    }
+  }
   if (rc == KG_OK) {
     b->gpu = gpu_name();
     b->grid = batched_grid(b->pair);
@@ -969,7 +1005,7 @@ kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count,
   if (rc == KG_OK) {
     std::vector<int> ids(count);
     for (int i = 0; i < count; ++i) ids[i] = i;
-    b->plan = make_plan(b->probs, ids, b->tune, b->pair, b->es);
+    b->plan = make_plan(b->probs, b->prep, ids, b->tune, b->pair, b->es);
     rc = devplan_alloc(b->dev, b->plan, s);
   }
   if (rc == KG_OK) {

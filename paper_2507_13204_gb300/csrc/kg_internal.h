@@ -120,7 +120,7 @@ bool qf_pair_supported(const kg_problem* p);
 kg_status pair_range_ok(kg_problem* p, const double* data, int64_t count, cudaStream_t s, bool* ok);
 kg_status qf_pair_range_ok(kg_problem* p, cudaStream_t s, bool* ok);
 kg_status qf_pair_prepare(kg_problem* p, cudaStream_t s);
-// dst[i] = float pair (h, l) of src[i] for i < count (count even, 16-byte aligned)
+// dst[i] = float pair (h, l) of src[i] for i < count (src and dst 16-byte aligned)
 kg_status pair_prepare(const double* src, void* dst, int64_t count, cudaStream_t s);
 int qf_pair_grid(const kg_problem* p, int* band);
 // Whether the warp-specialized pair gradient can run as one cooperative launch

@@ -580,24 +580,32 @@ __global__ void __launch_bounds__(512) qf_pair_reduce_kernel(const float4* __res
 }
 
 // The prepared copy of A: every double split into its float pair (h, l).
+// count doubles; an odd count's last one is split by thread 0 of block 0.
 __global__ void pair_prepare_kernel(const double2* __restrict__ A, float4* __restrict__ out,
-                                    int64_t n2) {
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+                                    int64_t count) {
+  const int64_t n2 = count / 2, stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
     const double2 v = __ldcs(A + i);
     const Pair p0 = split_f64(v.x), p1 = split_f64(v.y);
     __stcs(out + i, make_float4(p0.h, p0.l, p1.h, p1.l));
   }
+  if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const Pair q = split_f64(reinterpret_cast<const double*>(A)[count - 1]);
+    reinterpret_cast<float2*>(out)[count - 1] = make_float2(q.h, q.l);
+  }
 }
 
 // Sets ERRBIT_RANGE when some entry is outside the pair arithmetic's range.
-__global__ void pair_range_scan_kernel(const double2* __restrict__ p, int64_t n2, unsigned* err) {
+// count doubles; an odd count's last one is checked by thread 0 of block 0.
+__global__ void pair_range_scan_kernel(const double2* __restrict__ p, int64_t count, unsigned* err) {
   bool bad = false;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t n2 = count / 2, stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
     const double2 v = __ldcs(p + i);
     bad |= !pair_in_range(v.x) || !pair_in_range(v.y);
   }
+  if ((count & 1) && blockIdx.x == 0 && threadIdx.x == 0)
+    bad |= !pair_in_range(reinterpret_cast<const double*>(p)[count - 1]);
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) set_error(err, ERRBIT_RANGE);
 }
 
@@ -619,14 +627,14 @@ static size_t pair_smem(int n) {
 }
 
 // Scans `count` doubles once (create time) for values outside the pair range;
-// *ok is true if every value is representable.  Count must be even.
+// *ok is true if every value is representable.  data: 16-byte aligned.
 kg_status pair_range_ok(kg_problem* p, const double* data, int64_t count, cudaStream_t s, bool* ok) {
-  const int64_t n2 = count / 2;
+  const int64_t n2 = (count + 1) / 2;
   cudaError_t e = cudaMemsetAsync(p->err, 0, sizeof(unsigned), s);
   if (e != cudaSuccess) return cuda_fail(e, "pair range scan");
   int grid = (int)std::min<int64_t>((n2 + 255) / 256, (int64_t)num_sms() * 8);
   pair_range_scan_kernel<<<std::max(grid, 1), 256, 0, s>>>(reinterpret_cast<const double2*>(data),
-                                                         n2, p->err);
+                                                         count, p->err);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "pair range scan");
   unsigned h = 0;
   if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "pair range scan");
@@ -691,10 +699,10 @@ kg_status qf_pair_prepare(kg_problem* p, cudaStream_t s) {
 }
 
 kg_status pair_prepare(const double* src, void* dst, int64_t count, cudaStream_t s) {
-  const int64_t n2 = count / 2;
+  const int64_t n2 = (count + 1) / 2;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((n2 + 255) / 256, (int64_t)num_sms() * 8));
   pair_prepare_kernel<<<grid, 256, 0, s>>>(reinterpret_cast<const double2*>(src),
-                                           static_cast<float4*>(dst), n2);
+                                           static_cast<float4*>(dst), count);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? KG_OK : cuda_fail(e, "prepare float pairs");
 }

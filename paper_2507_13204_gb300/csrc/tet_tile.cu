@@ -276,7 +276,7 @@ struct TileArgs32 {
 };
 
 template <int MODE, bool STORE>
-__global__ void __launch_bounds__(TL_THREADS) tet_tile_f32_kernel(TileArgs32 a) {
+__global__ void __launch_bounds__(TL_THREADS, MODE == TS_HVP ? 3 : 4) tet_tile_f32_kernel(TileArgs32 a) {
   __shared__ __align__(16) float c_s[TL_THREADS / 32][2][TL_C];  // float4 stores
   __shared__ double red[32];
   constexpr bool HVP = MODE == TS_HVP;

@@ -108,6 +108,25 @@ def test_graph_replay_after_inputs_and_pointers_change(api, tmp_path, monkeypatc
         hx = x.cpu().numpy()
         ref = O.quadform_grad(h[1], hx) if h[0] == "dense" else O.tet_grad(h[1], h[2], hx)
         assert rel_l2(g.cpu().numpy(), ref[1]) <= TOL["f64"]
+    # bound buffers (pointer tables built once): the same results, then again after an
+    # in-place change of x; mixing the two call forms is an error
+    bound = batch.bind(xs2, fs, gxs2)
+    before = [g.clone() for g in gxs2]
+    batch.grad(bound)
+    batch.sync()
+    for a, b, h in zip(before, gxs2, host):
+        if h[0] == "dense":
+            assert torch.equal(a, b)
+    for x in xs2:
+        x.mul_(-1.0)
+    batch.grad(bound)
+    batch.sync()
+    for h, x, g in zip(host, xs2, gxs2):
+        hx = x.cpu().numpy()
+        ref = O.quadform_grad(h[1], hx) if h[0] == "dense" else O.tet_grad(h[1], h[2], hx)
+        assert rel_l2(g.cpu().numpy(), ref[1]) <= TOL["f64"]
+    with pytest.raises(ValueError):
+        batch.grad(bound, fs, gxs2)
 
 
 def test_batch_rejects_bad_inputs(api):
@@ -211,3 +230,48 @@ def test_full_4096_dense_512_tet_batch_sampled_against_oracle(api, tmp_path, mon
     batch.close()
     for p in probs:
         p.close()
+
+
+def test_batch_float_pair_copies_budget(api, tmp_path, monkeypatch):
+    # dense instances without their own float-pair copy (n < 1024) get one from the batch,
+    # largest first, within the budget; the copy holds the same pairs as the per-load
+    # split, so with the same tiles the results agree bitwise.  Odd n: an odd element count.
+    monkeypatch.setenv("KG_NO_AUTOTUNE", "1")
+    ns = [33, 255, 257, 511, 1000, 1024]
+    probs, host, xs, fs, gxs = _make(api, "f64", ns, [(3, 3, 2)], seed=11)
+    outs = []
+    for budget in (0, 1, 8 * 1000 * 1000 + 8):  # all, none, only the n = 1000 instance
+        batch = api.Batch(probs, budget_bytes=budget)
+        assert batch.config[0] == "pair"
+        f2 = [torch.empty_like(f) for f in fs]
+        g2 = [torch.full_like(g, 3.0) for g in gxs]
+        batch.grad(xs, f2, g2)
+        batch.sync()
+        for h, f, g in zip(host, f2, g2):
+            f_ref, g_ref = _oracle(h)
+            assert rel_scalar(f.item(), f_ref) <= TOL["f64"], h[0]
+            assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"], h[0]
+        outs.append([g.cpu().numpy() for g in g2[:len(ns)]])
+        batch.close()
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b)
+
+
+def test_batch_range_scan_sees_the_last_of_an_odd_count(api, tmp_path, monkeypatch):
+    # 33 x 33 = 1089 entries: the last one, below the pair range, makes the batch native
+    monkeypatch.setenv("KG_NO_AUTOTUNE", "1")
+    A, x = W.quadform_inputs(33, seed=2)
+    A[-1, -1] = 2.0 ** -70
+    p = api.QuadForm(torch.tensor(A, device="cuda"))
+    batch = api.Batch([p])
+    assert batch.config[0] == "native"
+    f = torch.empty((), dtype=torch.float64, device="cuda")
+    g = torch.empty(33, dtype=torch.float64, device="cuda")
+    batch.grad([torch.tensor(x, device="cuda")], [f], [g])
+    batch.sync()
+    f_ref, g_ref = O.quadform_grad(A, x)
+    assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+    assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+    batch.close()
+    p.close()
