@@ -8,9 +8,11 @@
 // sorted longest-first into a device work table.  Each CTA of the persistent
 // grid claims items from a device queue head (one atomicAdd per item) until
 // the table is exhausted.
-//   dense tile:  rows [r0, r0 + R): y_i by a row team (a warp for n <= 256,
-//                the CTA otherwise), ybar_i = 2 y_i, private xbar partial of
-//                the tile written to the instance's partial buffer;
+//   dense tile:  rows [r0, r0 + R): y_i by a row team (4 .. 256 threads,
+//                about 8 columns a thread), ybar_i = 2 y_i, private xbar
+//                partial of the tile written to the instance's partial buffer;
+//                on float-pair copies (pair batches) the rows arrive by bulk
+//                copies into a shared-memory ring, otherwise by plain loads;
 //   tet tile:    elements [e0, e0 + T): f_e and the scatter of c_e into gu (zeroed
 //                by a small kernel earlier in the graph): one global reduction per
 //                contribution, or warp-combined first with the WARP strategy.
@@ -83,6 +85,7 @@ struct BArgs {
   unsigned* err;
   const float4* logtab;
   LogConsts K;
+  int warpc;  // tet tiles: warp-combined atomics (else one per contribution)
 };
 
 // ------------------------------------------------------------- device ----
@@ -97,14 +100,10 @@ __device__ __forceinline__ void prefetch_range_l2(const void* p, size_t bytes) {
   }
 }
 
-// PREP: v holds the 8 bytes of a prepared float pair (h in the low word, l in
-// the high word), read as a double: two register moves instead of a split.
-template <bool PAIR, typename T, bool PREP = false>
+// The float pair (h, l) of v for pair arithmetic (zeros otherwise).
+template <bool PAIR, typename T>
 __device__ __forceinline__ void b_split(T v, float& h, float& l) {
-  if constexpr (PAIR && PREP) {
-    h = __int_as_float(__double2loint((double)v));
-    l = __int_as_float(__double2hiint((double)v));
-  } else if constexpr (PAIR) {
+  if constexpr (PAIR) {
     const Pair p = split_f64((double)v);
     h = p.h;
     l = p.l;
@@ -122,8 +121,9 @@ __device__ __forceinline__ void team_barrier(int team) {
   else named_barrier(1 + team, TEAM);
 }
 
-// Rows [w.start, w.start + w.count) of a dense instance; returns the tile's f.
-template <typename T, bool PAIR, int TEAM, bool PREP>
+// Rows [w.start, w.start + w.count) of a dense instance on its FP64 or FP32
+// data (pair batches: split on every load); returns the tile's f.
+template <typename T, bool PAIR, int TEAM>
 __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp, double* red,
                              bool& bad) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -171,7 +171,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
         for (int k = 0; k < B_CPT; ++k) {
           const int j = lt + k * TEAM;
           const T v = (k < cpt && vr[q] && j < n) ? __ldcs(Ar + j) : T(0);
-          b_split<PAIR, T, PREP>(v, ah[q][k], al[q][k]);
+          b_split<PAIR, T>(v, ah[q][k], al[q][k]);
         }
       }
       Acc y[2] = {acc_zero(), acc_zero()};
@@ -283,6 +283,9 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
         out[j] = s;
       }
     }
+    // in a pair batch wsp lies in the ring: order these generic accesses before
+    // the copies that will land there
+    fence_proxy_async_smem();
     // f of the tile: team leaders in team order
     Acc* ra = reinterpret_cast<Acc*>(red);
     __syncthreads();
@@ -319,6 +322,215 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
     __syncthreads();
     return tot;
   }
+}
+
+// ---- dense tiles of pair batches on float-pair copies: rows staged by bulk copies ----
+// A tile's rows are contiguous, so its data arrives by 1-D bulk copies (TMA)
+// into a ring of RING_S shared-memory slots, one iteration group (the 2 NT rows
+// one iteration of the teams takes, at most 32 KB: about B_CPT columns per
+// team thread) a slot, while the teams compute on the slot before: bytes in
+// flight without registers.  A copy covers the 16-byte aligned span around its
+// rows (a row starts 8 bytes off the boundary when n is odd; those copies are
+// the batch's own, allocated 16 bytes long), and the rows sit `off` bytes into
+// the slot.  All threads count the chunks the CTA has consumed (g), which
+// gives each slot's barrier phase across tiles; thread 0, the only one that
+// issues, counts the chunks issued (iss).  When a tile has no chunk left to
+// issue, the slots it frees take the first chunks of the CTA's next item
+// (claimed when this one started) if that is a ring tile too, so the copies
+// run on across the tile boundary.
+constexpr int RING_S = 3;
+constexpr int RING_SLOT = 32768 + 128;
+
+struct Ring {
+  unsigned char* slots;  // RING_S * RING_SLOT bytes
+  uint64_t* full;        // RING_S barriers: a slot's copy has landed
+};
+
+// The CTA's next item as ring chunks (thread 0 only); nchunks 0: not a ring tile.
+struct RingNext {
+  const double* src;   // its first row
+  int64_t chunk;       // entries a chunk (2 NT n)
+  int64_t total;       // entries of the item (count n)
+  int nchunks;
+};
+
+constexpr int RING_WS = 1024;  // Acc entries of the team combine's buffer (8 KB)
+
+__device__ __forceinline__ uint32_t ring_issue(const Ring& R, uint32_t g, const void* src, size_t bytes) {
+  const uintptr_t lo = reinterpret_cast<uintptr_t>(src) & ~uintptr_t(15);
+  const uintptr_t hi = (reinterpret_cast<uintptr_t>(src) + bytes + 15) & ~uintptr_t(15);
+  const int slot = (int)(g % RING_S);
+  mbar_arrive_expect_tx(&R.full[slot], (uint32_t)(hi - lo));
+  tma_load_1d(R.slots + slot * RING_SLOT, reinterpret_cast<const void*>(lo), (uint32_t)(hi - lo),
+              &R.full[slot]);
+  return (uint32_t)(reinterpret_cast<uintptr_t>(src) - lo);
+}
+
+// The dense_tile pair path on a prepared copy, reading its rows from the ring.
+// Returns the tile's f; sets `failed` (on all threads) when a copy did not land
+// within the wait limit, after waiting for the CTA's other copies in flight.
+// CPT > 0: the columns per team thread, ceil(n / TEAM), fixed at compile time
+// (no per-column tests but the last column's j < n); 0: at run time.
+template <int TEAM, int CPT>
+__device__ double dense_tile_ring(const BInst& I, const BItem& w, const Ring& R, uint32_t& g,
+                                  uint32_t& iss, const RingNext& nx, unsigned char* wsp, double* red,
+                                  bool& bad, bool& failed) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int n = I.n;
+  const double* __restrict__ A = static_cast<const double*>(I.d0);  // float pairs, 8 bytes an entry
+  const double* __restrict__ x = static_cast<const double*>(I.x);
+  constexpr int NT = BT / TEAM;
+  constexpr int W = TEAM < 32 ? TEAM : 32;  // lanes of the team inside one warp
+  const int lt = tid % TEAM, team = tid / TEAM;
+  constexpr int KM = CPT ? CPT : B_CPT;
+  const int cpt = CPT ? CPT : (n + TEAM - 1) / TEAM;
+  // column k of this thread is in the row: compile-time true below the last one
+  auto col_in = [&](int k, int j) { return (CPT && k < CPT - 1) || (k < cpt && j < n); };
+  float xh[KM], xl[KM];
+  Acc xbp[KM];
+#pragma unroll
+  for (int k = 0; k < KM; ++k) {
+    const int j = lt + k * TEAM;
+    const double xv = col_in(k, j) ? x[j] : 0.0;
+    bad |= !pair_in_range(xv);
+    b_split<true>(xv, xh[k], xl[k]);
+    xbp[k] = acc_zero();
+  }
+  Acc fp = acc_zero();
+  const int64_t r1 = w.start + w.count;
+  const int nchunks = (w.count + 2 * NT - 1) / (2 * NT);
+  auto chunk_src = [&](int c) { return A + (w.start + (int64_t)c * 2 * NT) * n; };
+  auto chunk_bytes = [&](int c) {
+    const int64_t left = r1 - (w.start + (int64_t)c * 2 * NT);
+    return (size_t)(left < 2 * NT ? left : 2 * NT) * n * 8;
+  };
+  const uint32_t off = (uint32_t)(reinterpret_cast<uintptr_t>(chunk_src(0)) & 15u);
+  // chunk row starts are n * 16 bytes apart: every chunk has the same offset
+  const uint32_t g0 = g;  // this tile's chunk c is the CTA's chunk g0 + c
+  if (tid == 0)  // (the first ones may have been issued by the tile before)
+    for (; (int)(iss - g0) < nchunks && iss - g0 < (uint32_t)RING_S; ++iss)
+      ring_issue(R, iss, chunk_src((int)(iss - g0)), chunk_bytes((int)(iss - g0)));
+  const bool upper = (lane & (W / 2)) != 0;  // keeps the second row
+  for (int c = 0; c < nchunks; ++c) {
+    const int slot = (int)(g % RING_S);
+    const bool ok = mbar_wait_bounded(&R.full[slot], (g / RING_S) & 1u);
+    const unsigned char* buf = R.slots + slot * RING_SLOT + off;
+    const int64_t row0 = w.start + (int64_t)c * 2 * NT;
+    const int64_t rr[2] = {row0 + team, row0 + NT + team};
+    const bool vr[2] = {ok && rr[0] < r1, ok && rr[1] < r1};
+    float ah[2][KM], al[2][KM];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const float2* Ar = reinterpret_cast<const float2*>(buf) + (int64_t)(q * NT + team) * n;
+#pragma unroll
+      for (int k = 0; k < KM; ++k) {
+        const int j = lt + k * TEAM;
+        const float2 v = (vr[q] && col_in(k, j)) ? Ar[j] : make_float2(0.f, 0.f);
+        ah[q][k] = v.x;
+        al[q][k] = v.y;
+      }
+    }
+    Acc y[2] = {acc_zero(), acc_zero()};
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      if (CPT || k < cpt) {
+        acc_fma(y[0], ah[0][k], al[0][k], xh[k], xl[k]);
+        acc_fma(y[1], ah[1][k], al[1][k], xh[k], xl[k]);
+      }
+    }
+    Acc keep = upper ? y[1] : y[0];
+    keep = acc_add(keep, shfl_xor_acc2(upper ? y[0] : y[1], W / 2));
+#pragma unroll
+    for (int o = W / 4; o > 0; o >>= 1) keep = acc_add(keep, shfl_xor_acc2(keep, o));
+    // teams wider than a warp exchange their warps' sums through shared memory
+    // (two buffers: chunk c + 1 writes the other while chunk c's are read)
+    constexpr int TW = TEAM > 32 ? TEAM / 32 : 1;
+    Acc* ra = reinterpret_cast<Acc*>(red) + (c & 1) * 2 * BW + team * 2 * TW;  // [TW][2]
+    if constexpr (TEAM > 32)
+      if ((lane & (W / 2 - 1)) == 0) ra[(warp % TW) * 2 + (upper ? 1 : 0)] = keep;
+    // one CTA barrier a chunk: the slot's entries are in registers now, so the
+    // slot is refilled here; it also publishes the warps' sums
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0)  // do not go on with a copy into this CTA's shared memory in flight
+        for (uint32_t h = g; h < iss; ++h) mbar_wait_bounded(&R.full[h % RING_S], (h / RING_S) & 1u);
+      failed = true;
+      __syncthreads();
+      return 0.0;
+    }
+    if (tid == 0 && iss - g0 < (uint32_t)(nchunks + nx.nchunks)) {
+      const int k = (int)(iss - g0);
+      if (k < nchunks) {
+        ring_issue(R, iss, chunk_src(k), chunk_bytes(k));
+      } else {  // the next item's chunk k - nchunks
+        const int64_t e0 = (int64_t)(k - nchunks) * nx.chunk, left = nx.total - e0;
+        ring_issue(R, iss, nx.src + e0, (size_t)(left < nx.chunk ? left : nx.chunk) * 8);
+      }
+      ++iss;
+    }
+    ++g;
+    if constexpr (TEAM > 32) {
+      keep = ra[upper ? 1 : 0];
+#pragma unroll
+      for (int q = 1; q < TW; ++q) keep = acc_add(keep, ra[q * 2 + (upper ? 1 : 0)]);
+    }
+    const Acc other = shfl_xor_acc2(keep, W / 2);
+    const Acc yt[2] = {upper ? other : keep, upper ? keep : other};
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      if (vr[q]) {
+        const Pair yq = acc_pair(yt[q]);
+        const Pair y2 = pair_mul(yq, yq);
+        fp = acc_add(fp, Acc{y2.h, y2.l});
+        const Pair yb{2.0f * yq.h, 2.0f * yq.l};  // exact
+#pragma unroll
+        for (int k = 0; k < KM; ++k)
+          if (CPT || k < cpt) acc_fma(xbp[k], ah[q][k], al[q][k], yb.h, yb.l);
+      }
+    }
+    if ((c & 7) == 7) {
+#pragma unroll
+      for (int k = 0; k < KM; ++k) acc_renorm(xbp[k]);
+    }
+  }
+  // combine the teams' partials in team order and store the tile's partial, in
+  // two halves of the columns through RING_WS entries (outside the ring, into
+  // which the next item's copies may be landing)
+  Acc* out = static_cast<Acc*>(I.partials) + (int64_t)w.tile * n;
+  if constexpr (NT == 1) {
+#pragma unroll
+    for (int k = 0; k < KM; ++k) {
+      const int j = lt + k * TEAM;
+      if (j < n) out[j] = xbp[k];
+    }
+  } else {
+    constexpr int H = B_CPT / 2;
+    static_assert(BT * H <= RING_WS, "the combine buffer holds half the columns of all teams");
+    Acc* ws = reinterpret_cast<Acc*>(wsp);  // [NT][TEAM * H]
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+#pragma unroll
+      for (int kk = 0; kk < H; ++kk)  // columns k >= KM are past the row's end: not read
+        if (half * H + kk < KM) ws[team * TEAM * H + lt + kk * TEAM] = xbp[half * H + kk < KM ? half * H + kk : 0];
+      __syncthreads();
+      for (int jj = tid; jj < TEAM * H; jj += BT) {
+        const int j = jj % TEAM + (half * H + jj / TEAM) * TEAM;
+        if (j < n) {
+          Acc s = ws[jj];
+          for (int t2 = 1; t2 < NT; ++t2) s = acc_add(s, ws[t2 * TEAM * H + jj]);
+          out[j] = s;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  Acc* ra = reinterpret_cast<Acc*>(red);
+  __syncthreads();
+  if (lt == 0) ra[team] = fp;
+  __syncthreads();
+  Acc tot = ra[0];
+  for (int t2 = 1; t2 < NT; ++t2) tot = acc_add(tot, ra[t2]);
+  __syncthreads();
+  return acc_to_double(tot);
 }
 
 // Elements [w.start, w.start + w.count) of a tet instance; returns the tile's f.
@@ -399,21 +611,47 @@ __device__ double tet_tile(const BInst& I, const BItem& w, const float4* tab, co
   }
 }
 
-template <typename T, bool PAIR, bool PREP>
+template <typename T, bool PAIR>
 __device__ __forceinline__ double dense_dispatch(const BInst& I, const BItem& w, unsigned char* wsp,
                                                  double* red, bool& bad) {
-  if constexpr (PREP && !PAIR) {
-    return 0.0;  // not instantiated: prepared copies exist for pair batches only
-  } else {
-    switch (I.team) {
-      case 4: return dense_tile<T, PAIR, 4, PREP>(I, w, wsp, red, bad);
-      case 8: return dense_tile<T, PAIR, 8, PREP>(I, w, wsp, red, bad);
-      case 16: return dense_tile<T, PAIR, 16, PREP>(I, w, wsp, red, bad);
-      case 32: return dense_tile<T, PAIR, 32, PREP>(I, w, wsp, red, bad);
-      case 64: return dense_tile<T, PAIR, 64, PREP>(I, w, wsp, red, bad);
-      case 128: return dense_tile<T, PAIR, 128, PREP>(I, w, wsp, red, bad);
-      default: return dense_tile<T, PAIR, BT, PREP>(I, w, wsp, red, bad);
-    }
+  switch (I.team) {
+    case 4: return dense_tile<T, PAIR, 4>(I, w, wsp, red, bad);
+    case 8: return dense_tile<T, PAIR, 8>(I, w, wsp, red, bad);
+    case 16: return dense_tile<T, PAIR, 16>(I, w, wsp, red, bad);
+    case 32: return dense_tile<T, PAIR, 32>(I, w, wsp, red, bad);
+    case 64: return dense_tile<T, PAIR, 64>(I, w, wsp, red, bad);
+    case 128: return dense_tile<T, PAIR, 128>(I, w, wsp, red, bad);
+    default: return dense_tile<T, PAIR, BT>(I, w, wsp, red, bad);
+  }
+}
+
+// The team is the smallest power of two (>= 4) with 8 columns a thread, so
+// above 4 threads a team thread has 5 to 8 columns.
+template <int TEAM>
+__device__ __forceinline__ double dense_ring_cpt(const BInst& I, const BItem& w, const Ring& R, uint32_t& g,
+                                                 uint32_t& iss, const RingNext& nx, unsigned char* wsp,
+                                                 double* red, bool& bad, bool& failed) {
+  switch ((I.n + TEAM - 1) / TEAM) {
+    case 5: return dense_tile_ring<TEAM, 5>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    case 6: return dense_tile_ring<TEAM, 6>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    case 7: return dense_tile_ring<TEAM, 7>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    case 8: return dense_tile_ring<TEAM, 8>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    default: return dense_tile_ring<TEAM, 0>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+  }
+}
+
+__device__ __forceinline__ double dense_ring_dispatch(const BInst& I, const BItem& w, const Ring& R,
+                                                      uint32_t& g, uint32_t& iss, const RingNext& nx,
+                                                      unsigned char* wsp, double* red, bool& bad,
+                                                      bool& failed) {
+  switch (I.team) {
+    case 4: return dense_tile_ring<4, 0>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    case 8: return dense_ring_cpt<8>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    case 16: return dense_ring_cpt<16>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    case 32: return dense_ring_cpt<32>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    case 64: return dense_ring_cpt<64>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    case 128: return dense_ring_cpt<128>(I, w, R, g, iss, nx, wsp, red, bad, failed);
+    default: return dense_ring_cpt<BT>(I, w, R, g, iss, nx, wsp, red, bad, failed);
   }
 }
 
@@ -448,31 +686,62 @@ __device__ void finalize(const BInst& I, double* red) {
   }
 }
 
-template <typename T, bool PAIR, bool WARPC>
-__global__ void __launch_bounds__(BT) batched_kernel(BArgs a) {
+template <typename T, bool PAIR>
+__global__ void __launch_bounds__(BT, 2) batched_kernel(BArgs a) {
+  // PAIR: [log table][ring: RING_S slots][ring combine buffer][red][ring barriers];
+  // the other dense tiles of a pair batch combine inside the ring (idle then).
+  // Otherwise [wsp][red].
   extern __shared__ __align__(16) unsigned char smem[];
   float4* tab = reinterpret_cast<float4*>(smem);
   unsigned char* wsp = smem + (PAIR ? kLogTableSize * sizeof(float4) : 0);
-  double* red = reinterpret_cast<double*>(wsp + (size_t)BT * B_CPT * 8);
+  unsigned char* rws = wsp + (PAIR ? (size_t)RING_S * RING_SLOT : 0);
+  double* red = reinterpret_cast<double*>(PAIR ? rws + RING_WS * sizeof(Acc) : wsp + (size_t)BT * B_CPT * 8);
+  Ring R{wsp, reinterpret_cast<uint64_t*>(red + 64)};
+  uint32_t g = 0, iss = 0;  // ring chunks consumed by this CTA; issued (thread 0)
   __shared__ int s_item, s_last;
   const int tid = threadIdx.x;
   if constexpr (PAIR) {
     for (int i = tid; i < kLogTableSize; i += BT) tab[i] = a.logtab[i];
+    if (tid == 0) {
+      for (int i = 0; i < RING_S; ++i) mbar_init(&R.full[i], 1);
+      fence_barrier_init();
+    }
   }
+  bool bad = false, failed = false;
+  // items are claimed one ahead: the next one's first copies can be issued
+  // during this one (pair batches)
+  if (tid == 0) s_item = (int)atomicAdd(&a.head[0], 1u);
   __syncthreads();
-  bool bad = false;
+  int it = s_item;
   for (;;) {
-    if (tid == 0) s_item = (int)atomicAdd(&a.head[0], 1u);
-    __syncthreads();
-    const int it = s_item;
-    __syncthreads();
+    __syncthreads();  // every thread has read s_item
     if (it >= a.nitems) break;
+    RingNext nx{nullptr, 0, 0, 0};
+    if (tid == 0) {
+      const int nit = (int)atomicAdd(&a.head[0], 1u);
+      s_item = nit;
+      if (PAIR && nit < a.nitems) {
+        const BItem wn = a.items[nit];
+        const BInst& In = a.insts[wn.inst];
+        if (In.kind == BK_DENSE && In.prep) {
+          const int64_t rows = 2 * (BT / In.team);
+          nx.src = static_cast<const double*>(In.d0) + wn.start * (int64_t)In.n;
+          nx.chunk = rows * In.n;
+          nx.total = (int64_t)wn.count * In.n;
+          nx.nchunks = (int)((wn.count + rows - 1) / rows);
+        }
+      }
+    }
     const BItem w = a.items[it];
     const BInst I = a.insts[w.inst];
-    if (tid == 0) {  // the tile's contiguous data into L2 while the first loads are in flight
+    // the tile's contiguous data into L2 while the first loads are in flight (not
+    // for the ring's tiles: their copies stream it, and whole-tile prefetches of
+    // every CTA exceed L2 and are evicted before use)
+    if (tid == 0) {
       if (I.kind == BK_DENSE) {
-        prefetch_range_l2(static_cast<const T*>(I.d0) + w.start * (int64_t)I.n,
-                          (size_t)w.count * I.n * sizeof(T));
+        if (!(PAIR && I.prep))
+          prefetch_range_l2(static_cast<const T*>(I.d0) + w.start * (int64_t)I.n,
+                            (size_t)w.count * I.n * sizeof(T));
       } else {
         prefetch_range_l2(static_cast<const int4*>(I.d0) + w.start, (size_t)w.count * 16);
         prefetch_range_l2(static_cast<const T*>(I.d1) + w.start * 12, (size_t)w.count * 12 * sizeof(T));
@@ -481,11 +750,23 @@ __global__ void __launch_bounds__(BT) batched_kernel(BArgs a) {
     double ft;
     const bool prep = PAIR && I.prep;
     if (I.kind == BK_DENSE) {
-      ft = prep ? dense_dispatch<T, PAIR, true>(I, w, wsp, red, bad)
-                : dense_dispatch<T, PAIR, false>(I, w, wsp, red, bad);
+      if constexpr (PAIR) {
+        ft = prep ? dense_ring_dispatch(I, w, R, g, iss, nx, rws, red, bad, failed)
+                  : dense_dispatch<T, PAIR>(I, w, wsp, red, bad);
+        if (failed) {  // a copy did not land: this CTA leaves the queue
+          if (tid == 0) set_error(a.err, ERRBIT_TIMEOUT);
+          break;
+        }
+      } else {
+        ft = dense_dispatch<T, PAIR>(I, w, wsp, red, bad);
+      }
     } else {
-      ft = prep ? tet_tile<T, PAIR, WARPC, true>(I, w, tab, a.K, red, bad)
-                : tet_tile<T, PAIR, WARPC, false>(I, w, tab, a.K, red, bad);
+      if (a.warpc)
+        ft = prep ? tet_tile<T, PAIR, true, true>(I, w, tab, a.K, red, bad)
+                  : tet_tile<T, PAIR, true, false>(I, w, tab, a.K, red, bad);
+      else
+        ft = prep ? tet_tile<T, PAIR, false, true>(I, w, tab, a.K, red, bad)
+                  : tet_tile<T, PAIR, false, false>(I, w, tab, a.K, red, bad);
     }
     if (tid == 0) I.fpart[w.tile] = ft;
     __threadfence();
@@ -497,6 +778,7 @@ __global__ void __launch_bounds__(BT) batched_kernel(BArgs a) {
       finalize<T, PAIR>(I, red);
       if (tid == 0) *I.done = 0u;
     }
+    it = s_item;  // written by thread 0 before the barriers above
   }
   if (bad) set_error(a.err, ERRBIT_RANGE);
   if (tid == 0) {  // the last CTA to leave resets the queue for the next replay
@@ -527,7 +809,10 @@ using namespace kg;
 namespace {
 
 size_t batched_smem(bool pair) {
-  return (pair ? kLogTableSize * sizeof(float4) : 0) + (size_t)BT * B_CPT * 8 + 64 * sizeof(double);
+  if (pair)
+    return kLogTableSize * sizeof(float4) + (size_t)RING_S * RING_SLOT + RING_WS * sizeof(Acc) +
+           64 * sizeof(double) + RING_S * sizeof(uint64_t);
+  return (size_t)BT * B_CPT * 8 + 64 * sizeof(double);
 }
 
 int bucket_of(int64_t v) {
@@ -709,27 +994,33 @@ kg_status devplan_alloc(DevPlan& D, Plan& P, cudaStream_t s) {
   return KG_OK;
 }
 
+// The pair kernels' shared memory (the ring) is above the 48 KB default: raise
+// their limit before the first occupancy query or launch.
+cudaError_t batched_smem_attrs() {
+  return cudaFuncSetAttribute(batched_kernel<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)batched_smem(true));
+}
+
 int batched_grid(bool pair) {
   int per = 0, dev = 0;
   cudaGetDevice(&dev);
   const size_t smem = batched_smem(pair);
   cudaError_t e;
   if (pair)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, true, true>, BT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, true>, BT, smem);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, false, true>, BT, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batched_kernel<double, false>, BT, smem);
   if (e != cudaSuccess || per < 1) per = 2;
   return num_sms() * std::min(per, 4);
 }
 
 // Launches the zero kernel (tet gradients) and the persistent kernel on s.
-template <bool WARPC>
 static void launch_batched(int dtype, bool pair, int grid, size_t smem, cudaStream_t s, const BArgs& a) {
   if (dtype == KG_F64) {
-    if (pair) batched_kernel<double, true, WARPC><<<grid, BT, smem, s>>>(a);
-    else batched_kernel<double, false, WARPC><<<grid, BT, smem, s>>>(a);
+    if (pair) batched_kernel<double, true><<<grid, BT, smem, s>>>(a);
+    else batched_kernel<double, false><<<grid, BT, smem, s>>>(a);
   } else {
-    batched_kernel<float, false, WARPC><<<grid, BT, smem, s>>>(a);
+    batched_kernel<float, false><<<grid, BT, smem, s>>>(a);
   }
 }
 
@@ -753,9 +1044,8 @@ kg_status launch_plan(const DevPlan& D, int dtype, bool pair, bool warp, unsigne
     kg_status rc = logtab_for_device(&a.logtab);
     if (rc != KG_OK) return rc;
   }
-  const size_t smem = batched_smem(pair);
-  if (warp) launch_batched<true>(dtype, pair, grid, smem, s, a);
-  else launch_batched<false>(dtype, pair, grid, smem, s, a);
+  a.warpc = warp ? 1 : 0;
+  launch_batched(dtype, pair, grid, batched_smem(pair), s, a);
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batched kernel");
   return KG_OK;
 }
@@ -835,8 +1125,11 @@ kg_status time_plan(kg_batch* b, const std::vector<int>& ids, const Tuning& tu, 
 }
 
 // Chooses rows (dense) / elements (tet) per item for every size bucket of the
-// batch: each candidate runs on up to 24 instances of the bucket; the fastest
-// wins.  Choices are cached by GPU name, kind, dtype, arithmetic and bucket.
+// batch: each candidate runs on a sample of the bucket's instances large
+// enough that the largest candidate still gives four items per CTA of the
+// persistent grid (or on all of them); the fastest wins.  A smaller sample
+// would favour small tiles for want of parallelism that the whole batch has.
+// Choices are cached by GPU name, kind, dtype, arithmetic and bucket.
 kg_status autotune(kg_batch* b, cudaStream_t s) {
   std::map<std::pair<int, int>, std::vector<int>> groups;  // (kind, bucket) -> instance ids
   for (int i = 0; i < (int)b->probs.size(); ++i) {
@@ -847,15 +1140,26 @@ kg_status autotune(kg_batch* b, cudaStream_t s) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   std::map<std::string, int> cache = cache_read();
   bool dirty = false;
-  // "k2": dense tiles of pair batches stream float-pair copies where the budget allows
-  const std::string prefix = b->gpu + "|k2|" + (b->dtype == KG_F64 ? "f64" : "f32") + "|" +
+  // "k3": dense tiles of pair batches stream float-pair copies through a ring; larger samples
+  const std::string prefix = b->gpu + "|k3|" + (b->dtype == KG_F64 ? "f64" : "f32") + "|" +
                              (b->pair ? "pair" : "native") + "|";
+  const std::vector<int> dense_cands{4, 8, 16, 32, 64, 128}, tet_cands{1024, 2048, 4096, 8192, 16384};
+  std::map<std::pair<int, int>, std::vector<int>> sample;
+  for (auto& g : groups) {
+    const int64_t biggest = g.first.first == BK_DENSE ? dense_cands.back() : tet_cands.back();
+    std::vector<int>& ids = sample[g.first];
+    int64_t items = 0;
+    for (int i : g.second) {
+      ids.push_back(i);
+      items += (b->probs[i]->m + biggest - 1) / biggest;
+      if (items >= 4 * (int64_t)b->grid) break;
+    }
+  }
   // scratch x / gx for the timing runs (zeros are valid inputs for both kinds)
   size_t need = 0;
-  for (auto& g : groups) {
+  for (auto& g : sample) {
     size_t sz = 0;
-    for (size_t k = 0; k < g.second.size() && k < 24; ++k)
-      sz += ((size_t)b->probs[g.second[k]]->n * b->es + 255) & ~size_t(255);
+    for (int i : g.second) sz += ((size_t)b->probs[i]->n * b->es + 255) & ~size_t(255);
     need = std::max(need, sz);
   }
   void *xbuf = nullptr, *gbuf = nullptr;
@@ -873,9 +1177,8 @@ kg_status autotune(kg_batch* b, cudaStream_t s) {
       (kind == BK_DENSE ? b->tune.dense_rows : b->tune.tet_elems)[bucket] = hit->second;
       continue;
     }
-    std::vector<int> ids(g.second.begin(), g.second.begin() + std::min<size_t>(24, g.second.size()));
-    std::vector<int> cands = kind == BK_DENSE ? std::vector<int>{4, 8, 16, 32, 64, 128}
-                                              : std::vector<int>{1024, 2048, 4096, 8192, 16384};
+    const std::vector<int>& ids = sample[g.first];
+    const std::vector<int>& cands = kind == BK_DENSE ? dense_cands : tet_cands;
     int best = cands[0];
     float best_ms = 1e30f;
     for (int c : cands) {
@@ -982,7 +1285,8 @@ kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count,
       const size_t bytes = 8 * (size_t)p->m * (size_t)p->n;
       if (bytes > budget) continue;
       void* q = nullptr;
-      if (dev_alloc(&q, bytes) != cudaSuccess) {
+      // 16 bytes beyond the end: the ring's copies read whole 16-byte units
+      if (dev_alloc(&q, bytes + 16) != cudaSuccess) {
         rc = fail(KG_ERR_OOM, "kg_batch_create: float-pair copy of A");
         break;
       }
@@ -991,6 +1295,10 @@ kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count,
       b->prep[i] = q;
       budget -= bytes;
     }
+  }
+  if (rc == KG_OK) {
+    cudaError_t e = batched_smem_attrs();
+    if (e != cudaSuccess) rc = cuda_fail(e, "kg_batch_create: kernel attributes");
   }
   if (rc == KG_OK) {
     b->gpu = gpu_name();
@@ -1009,13 +1317,7 @@ kg_status kg_batch_create(kg_batch** out, kg_problem* const* probs, int count,
     rc = devplan_alloc(b->dev, b->plan, s);
   }
   if (rc == KG_OK) {
-    cudaError_t e = cudaFuncSetAttribute(batched_kernel<double, true, true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)batched_smem(true));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(batched_kernel<double, true, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batched_smem(true));
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) rc = cuda_fail(e, "kg_batch_create");
   }
   if (rc != KG_OK) {
