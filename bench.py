@@ -573,19 +573,33 @@ class BatchedWL(Workload):
     compared with the per-instance launch loop."""
     unit = "grads/s"
 
-    def __init__(self, ndense=4096, ntet=512, arith="auto", strategy="auto"):
+    def __init__(self, ndense=4096, ntet=512, arith="auto", strategy="auto", nrange=None, limit=0):
+        """nrange (lo, hi), limit: only the first `limit` dense instances with lo <= n < hi of
+        the batch's draw, no tets (a profiling case of the same instances)."""
         self.ndense, self.ntet, self.arith, self.strategy = ndense, ntet, arith, strategy
+        self.nrange, self.limit = nrange, limit
+        self.ndraw, self.ntet_draw = ndense, ntet  # sizes of the draws (setup() counts the picks)
         self.es = 8
+
+    def instances(self):
+        """(indices k of the dense draw, their n_k, the tet boxes) of this batch."""
+        from paper_2507_13204_gb300 import workloads as W
+        drawn = W.batched_dense_sizes(self.ndraw)
+        ks = [k for k, n in enumerate(drawn)
+              if self.nrange is None or self.nrange[0] <= n < self.nrange[1]]
+        if self.limit:
+            ks = ks[:self.limit]
+        return ks, [int(drawn[k]) for k in ks], (W.batched_tet_boxes(self.ntet_draw) if self.ntet_draw else [])
 
     def setup(self, dev):
         import torch
         from paper_2507_13204_gb300 import api, workloads as W
-        sizes = W.batched_dense_sizes(self.ndense)
-        boxes = W.batched_tet_boxes(self.ntet)
+        ks, sizes, boxes = self.instances()
         self.sizes, self.boxes = sizes, boxes
+        self.ndense, self.ntet = len(sizes), len(boxes)
         probs, self.A, nx = [], [], []
         self.tets = []
-        for k, n in enumerate(sizes):
+        for k, n in zip(ks, sizes):
             A, x = W.batched_dense_device(k, int(n), dev)
             self.A.append((A, x))
             probs.append(api.QuadForm(A, arith=self.arith))
@@ -653,8 +667,10 @@ class BatchedWL(Workload):
         return self.probs[0]
 
     def config(self):
+        pick = ("" if self.nrange is None else
+                f", the first with {self.nrange[0]} <= n_k < {self.nrange[1]} of the 4096 drawn")
         return {"workload": f"batched: {self.ndense} dense ||A_k x_k||^2 (n_k log-uniform "
-                            f"[32, 2048]) + {self.ntet} tet meshes (1e3..1e5 tets), FP64, all "
+                            f"[32, 2048]{pick}) + {self.ntet} tet meshes (1e3..1e5 tets), FP64, all "
                             f"value+grads in one persistent launch (CUDA graph); float-pair "
                             f"copies of the data made at create",
                 "l2": f"inputs larger than L2 ({self.grad_bytes / 1e9:.1f} GB)",
@@ -776,6 +792,9 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
     if name == "batched":
         return BatchedWL(size or 4096, max(1, (size or 4096) // 8), arith=arith,
                          strategy=strategy or "auto")
+    if name == "batched_big":  # profiling case: the batch's first dense instances of 1024 <= n < 2048
+        return BatchedWL(4096, 0, arith=arith, strategy=strategy or "auto", nrange=(1024, 2048),
+                         limit=size or 96)
     if name == "dense":
         return DenseWL(size or 10000, "f64", arith=arith, m=rows or None)
     if name == "dense32":
@@ -810,16 +829,18 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
 # fingerprint it was taken with; after any change to them the field is null until re-measured.
 _CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_13204_gb300", "csrc")
 _TRAFFIC = {
-    ('dense', 'f64'): (815457536, ['quadform_pair.cu', 'kg_pair.cuh', 'kg_device.cuh'],
-                        '9cb7f542ed5dd002'),
+    ('dense', 'f64'): (817541120, ['quadform_pair.cu', 'kg_pair.cuh', 'kg_device.cuh'],
+                        '3f0c034b197a4bd3'),
     ('dense32', 'f32'): (406857984, ['quadform_f32.cu', 'kg_pair.cuh', 'kg_device.cuh'],
                           '7a908754a44fcb95'),
     ('tet', 'f64'): (711262976, ['tet_pair.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
                       '912296069bea1346'),
-    ('tet32', 'f32'): (469311232, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
-                        '81897ebbcc4c3357'),
-    ('tetcsr', 'f64'): (787844864, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
-                         '81897ebbcc4c3357'),
+    ('tet32', 'f32'): (469515264, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                        '5eea88b0d7f6e213'),
+    ('tetcsr', 'f64'): (788067328, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                         '5eea88b0d7f6e213'),
+    ('batched', 'f64'): (18535728384, ['batched.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                          '9badcfaa3c454dc8'),
 }
 
 
@@ -1206,14 +1227,13 @@ def run_reference(args, rank, world):
                   f"{wl.a}^3 mesh per step, scaled to the full mesh")
         to_value = lambda s: 1.0 / (s * wl.ne / ne)
     elif isinstance(wl, BatchedWL):
-        sizes = W.batched_dense_sizes(wl.ndense)
-        boxes = W.batched_tet_boxes(wl.ntet)
+        ks, sizes, boxes = wl.instances()
         wl.count = len(sizes) + len(boxes)
         wl.grad_bytes = (sum(8 * (int(n) * int(n) + 2 * int(n)) for n in sizes)
                          + sum(6 * a * b * c * (16 + 96) + 2 * (a + 1) * (b + 1) * (c + 1) * 8
                                for a, b, c in boxes))
-        nd, nt = 16, 2  # the batch's 8 : 1 mix of dense and tet instances
-        dense = [W.batched_dense_instance(k, int(sizes[k])) for k in range(nd)]
+        nd, nt = 16, min(2, len(boxes))  # the batch's 8 : 1 mix of dense and tet instances
+        dense = [W.batched_dense_instance(ks[i], sizes[i]) for i in range(min(nd, len(ks)))]
         tets = [W.batched_tet_instance(k, boxes[k]) for k in range(nt)]
 
         def fn():

@@ -18,7 +18,7 @@ def test_traffic_reported_only_at_default_sizes_and_matching_fingerprint():
         same = bench.source_fingerprint(files) == fp
         assert bench.recorded_traffic(wl, dt, True) == (nbytes if same else None)
         assert bench.recorded_traffic(wl, dt, False) is None
-    assert bench.recorded_traffic("batched", "f64", True) is None
+    assert bench.recorded_traffic("batched_big", "f64", True) is None  # no capture recorded
 
 
 def test_fingerprint_matches_when_sources_are_restored(tmp_path, monkeypatch):

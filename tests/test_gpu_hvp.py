@@ -6,7 +6,7 @@ import torch
 
 from oracle import oracle as O
 from paper_2507_13204_gb300 import workloads as W
-from tests.helpers import TOL, f32_round, rel_l2
+from tests.helpers import TOL, f32_round, rel_l2, rel_scalar
 
 pytestmark = pytest.mark.gpu
 
@@ -54,6 +54,31 @@ def test_tet_hvp_f32_and_accumulate(api):
           torch.tensor(v, dtype=torch.float32, device="cuda"), hv=hv, accumulate=True)
     p.sync()
     assert rel_l2(hv.cpu().numpy().astype(np.float64) - 2.0, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("strategy", ["tile", "csr"])
+def test_tet_hvp_and_grad_f32_half_scattered_element_order(api, strategy):
+    # the first half of the elements in mesh order (tiles of about 25 distinct vertices: u
+    # gathered once per tile vertex), the second half in random order (tiles of more than 32
+    # distinct vertices: gathered through conn); both in one call
+    mesh = W.tet_mesh(10, jitter_seed=5, perm_seed=6)
+    h = mesh.ne // 2
+    order = np.concatenate([np.arange(h), h + np.random.default_rng(7).permutation(mesh.ne - h)])
+    conn = np.ascontiguousarray(mesh.conn[order])
+    G32 = f32_round(np.ascontiguousarray(mesh.G[order]))
+    rng = np.random.default_rng(43)
+    u, v = f32_round(rng.uniform(-1, 1, mesh.nv)), f32_round(rng.uniform(-1, 1, mesh.nv))
+    p = api.TetEnergy(torch.tensor(conn, device="cuda"), torch.tensor(G32, dtype=torch.float32, device="cuda"),
+                      mesh.nv, strategy=strategy)
+    assert p.config[0] == strategy
+    ut, vt = torch.tensor(u, dtype=torch.float32, device="cuda"), torch.tensor(v, dtype=torch.float32, device="cuda")
+    hv = p.hvp(ut, vt)
+    f, g = p.grad(ut)
+    p.sync()
+    f_ref, g_ref = O.tet_grad(conn, G32, u)
+    assert rel_l2(hv.cpu().numpy(), O.tet_hvp(conn, G32, u, v)) <= TOL["f32"]
+    assert rel_scalar(f.item(), f_ref) <= TOL["f32"]
+    assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f32"]
 
 
 def test_tet_hvp_full_mesh_f64(api):
