@@ -452,7 +452,11 @@ __global__ void __launch_bounds__(WS_THREADS, 1) qf_pair_ws_kernel(QpArgs a) {
       for (int k = 0; k < KPD; ++k) {
         const int jp = t + TD * k;
         if (TD * (k + 1) <= 2 * H || jp < 2 * H) {  // the test is compiled for the last k only
-          const float4 q = jp < H ? buf0[jp] : buf1[jp - H];
+          // which chunk: known at compile time for all k but the one whose
+          // threads straddle the chunk boundary
+          const float4 q = TD * (k + 1) <= H ? buf0[jp]
+                           : TD * k >= H     ? buf1[jp - H]
+                                             : (jp < H ? buf0[jp] : buf1[jp - H]);
           acc_fma(yc[2 * (k & 1)], q.x, q.y, xh[k][0], xl[k][0]);
           acc_fma(yc[2 * (k & 1) + 1], q.z, q.w, xh[k][1], xl[k][1]);
         }
