@@ -336,6 +336,22 @@ class SparseWL(Workload):
         self.g_pin = torch.empty(self.n, dtype=td).pin_memory()
         self.f_pin = torch.empty((), dtype=td).pin_memory()
 
+    def l2_record(self, ms_grad, kernel_ms, strategy, box):
+        """The bound of random access: every stored entry costs a gather of x in the
+        forward and, in the reverse, a reduction into x-bar (ATOMIC) or a gather of y
+        (the CSC strategy).  Their least time at this run's measured rates, against the
+        step and the dominant kernel."""
+        wide = self.dtype == "f64"  # FP64: 8-byte values (float pairs or doubles)
+        g = box["fp64_gather_gops" if wide else "fp32_gather_gops"] * 1e9
+        r = box["fp64_red_gops" if wide else "fp32_red_gops"] * 1e9
+        rev = r if strategy == "atomic" else g
+        t_min_ms = (self.nnz / g + self.nnz / rev) * 1e3
+        return {"accesses_per_step": 2 * self.nnz, "gather_gops": round(g / 1e9, 1),
+                "reverse": "red" if strategy == "atomic" else "gather",
+                "reverse_gops": round(rev / 1e9, 1), "least_ms": round(t_min_ms, 5),
+                "frac_of_step": round(t_min_ms / ms_grad, 4),
+                "frac_of_kernel": round(t_min_ms / kernel_ms, 4) if strategy == "atomic" else None}
+
     def step(self):
         self.p.grad(self.xt, gx=self.gx, f=self.f)
 
@@ -1095,6 +1111,8 @@ def main():
         "launches_per_step": {"grad": launches_per_step, "eval": launches_eval},
         "clocks": clk,
         **({"native_f64": native} if native else {}),
+        **({"l2_random": wl.l2_record(ms_grad, per_launch_ms, strategy, box)}
+           if isinstance(wl, SparseWL) and "error" not in box else {}),
         "box": box,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -358,8 +358,9 @@ kg_status kg_check_bounded_wait(kg_problem *p, uint64_t limit_ns, kg_stream s);
  * (and motivate the float-pair arithmetic), measured by small kernels of the
  * library: eight independent register FMA chains per thread over 4 CTAs of
  * 256 threads per SM (FP64, FP32; FP64 log1p and division in the same
- * pattern), and red.global.add to pseudo-random slots of an 8 MiB array
- * (FP64, FP32).  Best of three timed launches each, after a
+ * pattern), red.global.add to pseudo-random slots of an 8 MiB array
+ * (FP64, FP32), and independent loads from the same slots (FP64, FP32; eight
+ * in flight a thread).  Best of three timed launches each, after a
  * warm-up.  Allocates and frees an 8 MiB scratch array and synchronises `s`
  * (a characterisation call, not a per-call entry point).  No passage: device
  * characterisation for the roofline. */
@@ -372,6 +373,8 @@ typedef struct {
   double fp64_div_gops;   /* FP64 division, the same pattern, 1e9/s */
   int sms;                /* streaming multiprocessors */
   int l2_bytes;           /* L2 cache size */
+  double fp64_gather_gops; /* FP64 loads from random L2-resident slots, 1e9/s */
+  double fp32_gather_gops; /* FP32 loads, same pattern, 1e9/s */
 } kg_box_rates;
 kg_status kg_measure_box(kg_box_rates *out, kg_stream s);
 

@@ -44,7 +44,8 @@ class kg_box_rates(ctypes.Structure):
     _fields_ = [("fp64_fma_tflops", ctypes.c_double), ("fp32_fma_tflops", ctypes.c_double),
                 ("fp64_red_gops", ctypes.c_double), ("fp32_red_gops", ctypes.c_double),
                 ("fp64_log1p_gops", ctypes.c_double), ("fp64_div_gops", ctypes.c_double),
-                ("sms", ctypes.c_int), ("l2_bytes", ctypes.c_int)]
+                ("sms", ctypes.c_int), ("l2_bytes", ctypes.c_int),
+                ("fp64_gather_gops", ctypes.c_double), ("fp32_gather_gops", ctypes.c_double)]
 
 
 class KGError(RuntimeError):

@@ -7,7 +7,9 @@
 //   - FP64 log1p and division rates, in the same chained pattern;
 //   - FP64 and FP32 reduction rates: every thread issues red.global.add to
 //     pseudo-random slots (xorshift) of an 8 MiB array, the scatter-add pattern
-//     of the tet and sparse gradients at an L2-resident footprint.
+//     of the tet and sparse gradients at an L2-resident footprint;
+//   - FP64 and FP32 gather rates: the same slots read by independent loads
+//     (eight in flight a thread), the sparse forward's x gathers.
 // Each kernel is timed with CUDA events after one warm-up launch (best of
 // three).  The results are kept live by a store that the data never triggers
 // (the compiler cannot prove it), so the loops are not removed.
@@ -81,6 +83,26 @@ __global__ void __launch_bounds__(kBoxBlock) red_rate_kernel(T* slots, uint32_t 
   }
 }
 
+template <typename T>
+__global__ void __launch_bounds__(kBoxBlock) gather_rate_kernel(const T* __restrict__ slots, uint32_t mask,
+                                                                int per_thread, T* sink) {
+  uint32_t x = 0x7F4A7C15u ^ (blockIdx.x * kBoxBlock + threadIdx.x) * 2654435761u;
+  T acc = 0;
+  for (int k = 0; k < per_thread; k += kChains) {
+    T v[kChains];
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) {
+      x ^= x << 13;
+      x ^= x >> 17;
+      x ^= x << 5;
+      v[c] = __ldg(slots + (x & mask));
+    }
+#pragma unroll
+    for (int c = 0; c < kChains; ++c) acc += v[c];
+  }
+  if (acc == (T)-1234.5) sink[0] = acc;  // the slots hold zeros: never true
+}
+
 template <typename K>
 kg_status time_best(K launch, cudaStream_t s, float* best_ms) {
   cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -147,6 +169,17 @@ extern "C" kg_status kg_measure_box(kg_box_rates* out, kg_stream stream) {
     rc = time_best([&] { red_rate_kernel<float><<<rgrid, kBoxBlock, 0, s>>>(
                              static_cast<float*>(buf), kSlots - 1, per); }, s, &ms);
   if (rc == KG_OK) out->fp32_red_gops = reds / (ms * 1e-3) / 1e9;
+  // the red kernels left the slots at small integers; the gathers want zeros
+  if (rc == KG_OK && cudaMemsetAsync(buf, 0, kSlots * sizeof(double), s) != cudaSuccess)
+    rc = fail(KG_ERR_CUDA, "kg_measure_box: scratch reset");
+  if (rc == KG_OK)
+    rc = time_best([&] { gather_rate_kernel<double><<<rgrid, kBoxBlock, 0, s>>>(
+                             static_cast<const double*>(buf), kSlots - 1, per, static_cast<double*>(buf)); }, s, &ms);
+  if (rc == KG_OK) out->fp64_gather_gops = reds / (ms * 1e-3) / 1e9;
+  if (rc == KG_OK)
+    rc = time_best([&] { gather_rate_kernel<float><<<rgrid, kBoxBlock, 0, s>>>(
+                             static_cast<const float*>(buf), kSlots - 1, per, static_cast<float*>(buf)); }, s, &ms);
+  if (rc == KG_OK) out->fp32_gather_gops = reds / (ms * 1e-3) / 1e9;
   const int itl = 64;
   if (rc == KG_OK)
     rc = time_best([&] { log1p_rate_kernel<<<grid, kBoxBlock, 0, s>>>(static_cast<double*>(buf), itl); }, s,
