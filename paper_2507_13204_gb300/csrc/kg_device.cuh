@@ -145,6 +145,34 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// Grid barrier of a cooperative launch (every CTA resident), for thread 0 of
+// each CTA after a __syncthreads: the CTA's writes are made visible, it counts
+// itself in at arrive[0] and waits, bounded, until every CTA has.  Returns
+// false (ERRBIT_TIMEOUT set in err) when the wait gives up.
+__device__ __forceinline__ bool grid_arrive_and_wait(unsigned* arrive, unsigned* err, unsigned bit) {
+  __threadfence();
+  atomicAdd(arrive, 1u);
+  const uint64_t t0 = global_ns();
+  while (ld_acquire_u32(arrive) < gridDim.x) {
+    if (global_ns() - t0 > kWaitLimitNs) {
+      set_error(err, bit);
+      return false;
+    }
+  }
+  __threadfence();
+  return true;
+}
+
+// Thread 0 counts the CTA out of the barrier's work at depart[0]; the last CTA
+// resets both counters for the next launch.
+__device__ __forceinline__ void grid_depart(unsigned* arrive, unsigned* depart) {
+  __threadfence();
+  if (atomicAdd(depart, 1u) == gridDim.x - 1) {
+    *arrive = 0u;
+    *depart = 0u;
+  }
+}
+
 // In a kernel launched with programmatic stream serialization: blocks until
 // the preceding grid on the stream has completed and its memory operations
 // are visible (returns at once otherwise).

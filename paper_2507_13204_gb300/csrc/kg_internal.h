@@ -39,7 +39,7 @@ struct QfConfig {
   int grid = 1;     // CTAs
   int rows_per_cta = 1;
   int streamed = 0;  // 1: FP32 TMA-streamed kernel (quadform_f32.cu)
-  int coop = 0;      // 1: the float-pair gradient reduces its partials in one cooperative launch
+  int coop = 0;      // 1: the streamed gradient (pair, FP32) reduces its partials in one cooperative launch
 };
 
 struct kg_problem_impl;
@@ -126,6 +126,8 @@ int qf_pair_grid(const kg_problem* p, int* band);
 // Whether the warp-specialized pair gradient can run as one cooperative launch
 // (its whole grid resident at once); the test hook KG_TEST_NO_COOP=1 says no.
 bool qf_pair_coop_fits(const kg_problem* p);
+// The same for the FP32 streamed gradient (quadform_f32.cu).
+bool qf_f32_coop_fits(const kg_problem* p);
 kg_status qf_pair_eval(kg_problem* p, const void* x, void* f, cudaStream_t s);
 kg_status qf_pair_grad(kg_problem* p, const void* x, void* f, void* gx, const void* seed,
                        int accumulate, cudaStream_t s);

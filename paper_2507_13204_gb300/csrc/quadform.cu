@@ -366,8 +366,9 @@ kg_status qf_setup(kg_problem* p, cudaStream_t s) {
     c.grid = qf_f32_grid(p, &c.rows_per_cta);
     c.team = c.block = 512;
     kg_status rc = ws_common(p, c.grid, s);
-    if (rc != KG_OK) return rc;
-    return ws_alloc(p, &p->partials, 4 * (size_t)c.grid * p->n, "xbar partials (FP32)");
+    if (rc == KG_OK) rc = ws_alloc(p, &p->partials, 4 * (size_t)c.grid * p->n, "xbar partials (FP32)");
+    if (rc == KG_OK) c.coop = qf_f32_coop_fits(p) ? 1 : 0;
+    return rc;
   }
   if (p->strategy == KG_STRATEGY_AUTO) p->strategy = var >= 0 ? KG_STRATEGY_FUSED : KG_STRATEGY_TRANSPOSE;
   if (var < 0) {

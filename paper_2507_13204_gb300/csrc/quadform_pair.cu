@@ -349,21 +349,7 @@ __device__ __forceinline__ void ws_grid_reduce(const QpArgs& a, int npairs) {
   __shared__ Acc red[RED_PY][RED_CX][2];
   __shared__ double fred[32];
   __shared__ int go;
-  if (threadIdx.x == 0) {
-    __threadfence();  // this CTA's partials (ordered before by the barrier) first
-    atomicAdd(a.counter + 2, 1u);
-    bool ok = true;
-    const uint64_t t0 = global_ns();
-    while (ld_acquire_u32(a.counter + 2) < gridDim.x) {
-      if (global_ns() - t0 > kWaitLimitNs) {
-        set_error(a.err, ERRBIT_TIMEOUT);
-        ok = false;
-        break;
-      }
-    }
-    __threadfence();
-    go = ok;
-  }
+  if (threadIdx.x == 0) go = grid_arrive_and_wait(a.counter + 2, a.err, ERRBIT_TIMEOUT);
   __syncthreads();
   if (go) {
     const int nparts = gridDim.x;
@@ -374,13 +360,7 @@ __device__ __forceinline__ void ws_grid_reduce(const QpArgs& a, int npairs) {
     }
     if (blockIdx.x == 0 && a.f) reduce_f_partials(a.fpart, nparts, a.f, fred);
   }
-  if (threadIdx.x == 0) {
-    __threadfence();
-    if (atomicAdd(a.counter + 3, 1u) == gridDim.x - 1) {
-      a.counter[2] = 0u;
-      a.counter[3] = 0u;
-    }
-  }
+  if (threadIdx.x == 0) grid_depart(a.counter + 2, a.counter + 3);
 }
 
 template <int KP, bool GRIDRED>

@@ -264,3 +264,35 @@ def test_one_launch_and_two_launch_reductions_agree_bitwise(api, m, n, monkeypat
     assert rel_scalar(f1, f_ref) <= TOL["f64"] and rel_l2(g1, g_ref) <= TOL["f64"]
     assert f1 == f0 and np.array_equal(g1, g0) and np.array_equal(a1, a0)
     assert np.array_equal(a1, 0.25 + g1)
+
+
+@pytest.mark.parametrize("m,n", [(1, 1024), (777, 4100), (10000, 10000)])
+def test_f32_one_launch_and_two_launch_reductions_agree_bitwise(api, m, n, monkeypatch):
+    # FP32 streamed kernel: the reduction in the kernel's tail (one cooperative launch) and the
+    # separate reduce kernel (KG_TEST_NO_COOP=1 at create) add the partials in the same order
+    from paper_2507_13204_gb300 import _lib as L
+    A, x = W.quadform_inputs(n, m=m, seed=5 * m + n)
+    A, x = f32_round(A), f32_round(x)
+    f_ref, g_ref = O.quadform_grad(A, x, fbar=0.5)
+    At = torch.tensor(A, dtype=torch.float32, device="cuda")
+    xt = torch.tensor(x, dtype=torch.float32, device="cuda")
+    seed = torch.tensor(0.5, dtype=torch.float32, device="cuda")
+    out = {}
+    for coop in (1, 0):
+        if coop:
+            monkeypatch.delenv("KG_TEST_NO_COOP", raising=False)
+        else:
+            monkeypatch.setenv("KG_TEST_NO_COOP", "1")
+        p = api.QuadForm(At)
+        f, g = p.grad(xt, seed=seed)
+        launches = L.kg_last_launch_count()
+        g2 = torch.full_like(g, 0.25)
+        p.grad(xt, gx=g2, seed=seed, accumulate=True)
+        p.sync()
+        out[coop] = (f.item(), g.cpu().numpy(), g2.cpu().numpy(), launches)
+        p.close()
+    (f1, g1, a1, l1), (f0, g0, a0, l0) = out[1], out[0]
+    assert (l1, l0) == (1, 2)
+    assert rel_scalar(f1, f_ref) <= TOL["f32"] and rel_l2(g1, g_ref) <= TOL["f32"]
+    assert f1 == f0 and np.array_equal(g1, g0) and np.array_equal(a1, a0)
+    assert np.array_equal(a1, np.float32(0.25) + g1)
