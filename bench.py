@@ -845,18 +845,18 @@ def make_workload(name: str, arith: str, size: int = 0, rows: int = 0, strategy:
 # fingerprint it was taken with; after any change to them the field is null until re-measured.
 _CSRC = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2507_13204_gb300", "csrc")
 _TRAFFIC = {
-    ('dense', 'f64'): (817519104, ['quadform_pair.cu', 'kg_pair.cuh', 'kg_device.cuh'],
-                        '180f390ba11bf3f5'),
-    ('dense32', 'f32'): (406857984, ['quadform_f32.cu', 'kg_pair.cuh', 'kg_device.cuh'],
-                          '7a908754a44fcb95'),
-    ('tet', 'f64'): (711262976, ['tet_pair.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
-                      '912296069bea1346'),
-    ('tet32', 'f32'): (469515264, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
-                        '5eea88b0d7f6e213'),
-    ('tetcsr', 'f64'): (788067328, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
-                         '5eea88b0d7f6e213'),
-    ('batched', 'f64'): (18535728384, ['batched.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
-                          '9badcfaa3c454dc8'),
+    ('dense', 'f64'): (816908288, ['quadform_pair.cu', 'kg_pair.cuh', 'kg_device.cuh'],
+                       'f376193dfdbd63bd'),
+    ('dense32', 'f32'): (406167296, ['quadform_f32.cu', 'kg_pair.cuh', 'kg_device.cuh'],
+                         '3fea89b37a6236f9'),
+    ('tet', 'f64'): (711157760, ['tet_pair.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                     '33085ea1051816f5'),
+    ('tet32', 'f32'): (469459712, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                       '166f724fdbe0f6dd'),
+    ('tetcsr', 'f64'): (787957760, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                        '166f724fdbe0f6dd'),
+    ('batched', 'f64'): (18536587008, ['batched.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                         '58affb4ea7822c4f'),
 }
 
 
