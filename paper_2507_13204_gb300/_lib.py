@@ -62,6 +62,8 @@ _lib = None
 def lib():
     """Opens libkg.so (built by build.build() / __graft_entry__.build())."""
     global _lib
+    if _lib is not None:  # opened once; the lock only guards the first open
+        return _lib
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
@@ -123,10 +125,26 @@ def ptr(t) -> int | None:
     raise TypeError(f"cannot take the address of {type(t)}")
 
 
+_current_stream = None  # () -> raw cudaStream_t of torch's current stream, or None
+
+
+def _current_stream_fn():
+    import torch
+    if not torch.cuda.is_available():
+        return lambda: None
+    raw, dev = getattr(torch._C, "_cuda_getCurrentRawStream", None), getattr(torch._C, "_cuda_getDevice", None)
+    if raw is not None and dev is not None:  # a few microseconds less a call than current_stream()
+        return lambda: raw(dev())
+    return lambda: torch.cuda.current_stream().cuda_stream
+
+
 def stream_handle(stream) -> int | None:
+    """None: torch's current stream on the current device."""
+    global _current_stream
     if stream is None:
-        import torch
-        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+        if _current_stream is None:
+            _current_stream = _current_stream_fn()
+        return _current_stream()
     if isinstance(stream, int):
         return stream
     return stream.cuda_stream

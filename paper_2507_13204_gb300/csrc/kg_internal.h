@@ -31,6 +31,14 @@ cudaError_t dev_alloc(void** p, size_t bytes);
 
 int num_sms();
 
+// cudaFuncSetAttribute(fn, MaxDynamicSharedMemorySize, bytes), made once per
+// kernel, device and size: the per-call launch paths go through this.
+cudaError_t set_smem_once(const void* fn, int bytes);
+template <typename K>
+inline cudaError_t set_smem_once(K* fn, size_t bytes) {
+  return set_smem_once(reinterpret_cast<const void*>(fn), (int)bytes);
+}
+
 // Launch configuration of one dense row-team kernel.
 struct QfConfig {
   int block = 256;  // threads per CTA

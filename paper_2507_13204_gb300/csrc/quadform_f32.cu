@@ -307,7 +307,7 @@ static size_t f32_smem(int n) { return (size_t)2 * n * 4 + 4 * 8 + 2 * QF_CW * 4
 template <int QPT, bool FUSED, bool GRIDRED>
 static cudaError_t launch_f32(int grid, size_t smem, cudaStream_t s, const Qf32Args& a) {
   auto kern = qf_f32_kernel<QPT, FUSED, GRIDRED>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_once(kern, smem);
   if (e != cudaSuccess) return e;
   if constexpr (GRIDRED) {
     cudaLaunchConfig_t cfg = {};
@@ -346,7 +346,7 @@ static bool f32_coop_fits_q(int grid, size_t smem) {
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
     return false;
   auto kern = qf_f32_kernel<QPT, true, true>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+  if (set_smem_once(kern, smem) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, QF_CT, smem) != cudaSuccess) {
     cudaGetLastError();
     return false;

@@ -644,7 +644,7 @@ int qf_pair_grid(const kg_problem* p, int* band) {
 template <int PPT, bool FUSED, bool PREP>
 static cudaError_t launch_pair(int grid, size_t smem, cudaStream_t s, const QpArgs& a) {
   auto kern = qf_pair_kernel<PPT, FUSED, PREP>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = set_smem_once(kern, smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, QP_THREADS, smem, s>>>(a);
   return cudaGetLastError();
@@ -738,8 +738,7 @@ static cudaError_t launch_ws(int grid, cudaStream_t s, const QpArgs& a, bool fus
   cudaError_t e;
   if (fused) {
     auto kern = qf_pair_ws_kernel<KP, true>;
-    if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-      return e;
+    if ((e = set_smem_once(kern, smem)) != cudaSuccess) return e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(WS_THREADS);
@@ -753,8 +752,7 @@ static cudaError_t launch_ws(int grid, cudaStream_t s, const QpArgs& a, bool fus
     return cudaLaunchKernelEx(&cfg, kern, a);
   }
   auto kern = qf_pair_ws_kernel<KP, false>;
-  if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
-    return e;
+  if ((e = set_smem_once(kern, smem)) != cudaSuccess) return e;
   kern<<<grid, WS_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -776,7 +774,7 @@ static bool ws_coop_fits(int grid) {
       cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
     return false;
   auto kern = qf_pair_ws_kernel<KP, true>;
-  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws_smem(KP)) != cudaSuccess ||
+  if (set_smem_once(kern, ws_smem(KP)) != cudaSuccess ||
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, WS_THREADS, ws_smem(KP)) != cudaSuccess) {
     cudaGetLastError();
     return false;

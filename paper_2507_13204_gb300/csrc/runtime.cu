@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -89,6 +90,20 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
     if (target > 0 && n == target) return cudaErrorMemoryAllocation;
   }
   return cudaMalloc(p, bytes < 16 ? 16 : bytes);
+}
+
+cudaError_t set_smem_once(const void* fn, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> bytes set
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = done.find({fn, dev});
+  if (it != done.end() && it->second == bytes) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess) done[{fn, dev}] = bytes;
+  return e;
 }
 
 int num_sms() {
