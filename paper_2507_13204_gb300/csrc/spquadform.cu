@@ -370,11 +370,16 @@ static int sq_grid(int64_t work_rows, int tw) {
 }
 
 // Lanes per row (or column) team: the smallest power of two (2..32) whose
-// SQ_U-entry steps cover 1.5 x the average length in one step.
-static int team_for(double avg, int requested) {
+// SQ_U-entry steps cover `cover` x the average length in one step.  Measured on
+// the 2^20-row matrix with 8..24 entries a row: FP64 (float pairs) is fastest
+// at 8 lanes (cover 1.5: 185 us against 218 at 4 lanes); FP32 at 2 lanes (cover
+// 0.5: 168.6 / 167.0 us for the atomic / CSC gradient, against 175.2 / 208.1 at
+// 8): its cheaper arithmetic leaves the loads the bound, and narrower teams keep
+// more rows' gathers in flight.
+static int team_for(double avg, int requested, double cover) {
   if (requested) return requested;
   int tw = 2;
-  while (tw < 32 && (double)(tw * SQ_U) < 1.5 * avg) tw *= 2;
+  while (tw < 32 && (double)(tw * SQ_U) < cover * avg) tw *= 2;
   return tw;
 }
 
@@ -393,8 +398,9 @@ kg_status spq_setup(kg_problem* p, cudaStream_t s) {
   const int t = p->opt.team;
   if (t && t != 2 && t != 4 && t != 8 && t != 16 && t != 32)
     return fail(KG_ERR_UNSUPPORTED, "SPQUADFORM: team must be 2, 4, 8, 16 or 32");
-  p->sq_team = team_for((double)p->nnz / (double)p->m, t);
-  p->sq_col_team = team_for((double)p->nnz / (double)p->n, t);
+  const double cover = p->dtype == KG_F32 ? 0.5 : 1.5;
+  p->sq_team = team_for((double)p->nnz / (double)p->m, t, cover);
+  p->sq_col_team = team_for((double)p->nnz / (double)p->n, t, cover);
   const int grid = sq_grid(p->m, p->sq_team);
   kg_status rc = ws_common(p, grid, s);
   if (rc != KG_OK) return rc;
