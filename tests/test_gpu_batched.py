@@ -275,3 +275,20 @@ def test_batch_range_scan_sees_the_last_of_an_odd_count(api, tmp_path, monkeypat
     assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
     batch.close()
     p.close()
+
+
+def test_batch_tiny_and_odd_rows_through_the_ring(api, tmp_path, monkeypatch):
+    # rows of 8 .. 136 bytes: chunk starts 8 bytes off the 16-byte boundary (odd n), several
+    # chunks in one tile, instances of one row; in pair arithmetic on the batch's copies
+    monkeypatch.setenv("KG_TUNE_CACHE", str(tmp_path / "tune.json"))
+    ns = [1, 2, 3, 5, 7, 9, 17, 31]
+    probs, host, xs, fs, gxs = _make(api, "f64", ns, [], seed=21)
+    batch = api.Batch(probs)
+    assert batch.config[0] == "pair"
+    batch.grad(xs, fs, gxs)
+    batch.sync()
+    for h, f, g in zip(host, fs, gxs):
+        f_ref, g_ref = _oracle(h)
+        assert rel_scalar(f.item(), f_ref) <= TOL["f64"]
+        assert rel_l2(g.cpu().numpy(), g_ref) <= TOL["f64"]
+    batch.close()
