@@ -1143,7 +1143,7 @@ kg_status autotune(kg_batch* b, cudaStream_t s) {
   // "k3": dense tiles of pair batches stream float-pair copies through a ring; larger samples
   const std::string prefix = b->gpu + "|k3|" + (b->dtype == KG_F64 ? "f64" : "f32") + "|" +
                              (b->pair ? "pair" : "native") + "|";
-  const std::vector<int> dense_cands{4, 8, 16, 32, 64, 128}, tet_cands{1024, 2048, 4096, 8192, 16384};
+  const std::vector<int> dense_cands{4, 8, 16, 32, 64, 128, 256}, tet_cands{1024, 2048, 4096, 8192, 16384};
   std::map<std::pair<int, int>, std::vector<int>> sample;
   for (auto& g : groups) {
     const int64_t biggest = g.first.first == BK_DENSE ? dense_cands.back() : tet_cands.back();
