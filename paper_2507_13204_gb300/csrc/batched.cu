@@ -331,7 +331,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
 // team thread) a slot, while the teams compute on the slot before: bytes in
 // flight without registers.  A copy covers the 16-byte aligned span around its
 // rows (a row starts 8 bytes off the boundary when n is odd; those copies are
-// the batch's own, allocated 16 bytes long), and the rows sit `off` bytes into
+// the batch's own, allocated 16 bytes longer), and the rows sit `off` bytes into
 // the slot.  All threads count the chunks the CTA has consumed (g), which
 // gives each slot's barrier phase across tiles; thread 0, the only one that
 // issues, counts the chunks issued (iss).  When a tile has no chunk left to
