@@ -56,9 +56,11 @@ __device__ __forceinline__ T team_sum(T v, T* red, int par) {
     T* r = red + (par * nteams + team) * W;
     if ((threadIdx.x & 31) == 0) r[w] = v;
     __syncthreads();
-    T s = T(0);
+    // lane l takes warp l mod W's sum, and a butterfly over W lanes gives every lane the
+    // same total: log2(W) adds a thread instead of W (FP64 adds are scarce on GB300)
+    T s = r[(threadIdx.x & 31) % W];
 #pragma unroll
-    for (int i = 0; i < W; ++i) s += r[i];
+    for (int o = W / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return s;
   }
 }
