@@ -257,11 +257,13 @@ static const QfVariant kVariants[] = {
     {32, 4, 256},    // n <= 128: warp per row, 8 rows in flight per CTA
     {128, 8, 256},   // n <= 1024
     {256, 8, 256},   // n <= 2048
-    {512, 24, 512},  // n <= 12288: the whole CTA is one row team
+    {512, 20, 512},  // n <= 10240: the whole CTA is one row team (n = 1e4: no idle column slot)
+    {512, 24, 512},  // n <= 12288
 };
+constexpr int kNumVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 
 static int pick_variant(int64_t n, int team_hint) {
-  for (int v = 0; v < 4; ++v) {
+  for (int v = 0; v < kNumVariants; ++v) {
     if (team_hint && kVariants[v].team != team_hint) continue;
     if (n <= (int64_t)kVariants[v].team * kVariants[v].cpt_max) return v;
   }
@@ -293,7 +295,8 @@ static cudaError_t launch_team(int var, dim3 grid, cudaStream_t s, const QfArgs<
     case 0: go(qf_team_kernel<T, 32, 4, MODE>); break;
     case 1: go(qf_team_kernel<T, 128, 8, MODE>); break;
     case 2: go(qf_team_kernel<T, 256, 8, MODE>); break;
-    case 3: go(qf_team_kernel<T, 512, 24, MODE>); break;
+    case 3: go(qf_team_kernel<T, 512, 20, MODE>); break;
+    case 4: go(qf_team_kernel<T, 512, 24, MODE>); break;
     default: e = cudaErrorInvalidValue;
   }
   count_launch();
@@ -309,7 +312,8 @@ static cudaError_t launch_atomic(int var, dim3 grid, cudaStream_t s, const QfArg
     case 0: qf_atomic_adjoint_kernel<T, 32, 4><<<grid, v.block, 0, s>>>(a, gx); break;
     case 1: qf_atomic_adjoint_kernel<T, 128, 8><<<grid, v.block, 0, s>>>(a, gx); break;
     case 2: qf_atomic_adjoint_kernel<T, 256, 8><<<grid, v.block, 0, s>>>(a, gx); break;
-    case 3: qf_atomic_adjoint_kernel<T, 512, 24><<<grid, v.block, 0, s>>>(a, gx); break;
+    case 3: qf_atomic_adjoint_kernel<T, 512, 20><<<grid, v.block, 0, s>>>(a, gx); break;
+    case 4: qf_atomic_adjoint_kernel<T, 512, 24><<<grid, v.block, 0, s>>>(a, gx); break;
     default: return cudaErrorInvalidValue;
   }
   count_launch();
