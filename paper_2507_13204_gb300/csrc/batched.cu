@@ -121,6 +121,18 @@ __device__ __forceinline__ void team_barrier(int team) {
   else named_barrier(1 + team, TEAM);
 }
 
+// The team's sum of its TW warps' row sums ra[q * 2 + upper] (q < TW), for a
+// team wider than a warp: lane l takes warp l mod TW's and a butterfly over TW
+// lanes (inside the lane's half-warp, so over one row) gives every lane the
+// same total, with log2(TW) pair additions a thread instead of TW - 1.
+template <int TW>
+__device__ __forceinline__ Acc team_warps_sum(const Acc* ra, int lane, bool upper) {
+  Acc k = ra[(lane & (TW - 1)) * 2 + (upper ? 1 : 0)];
+#pragma unroll
+  for (int o = TW / 2; o > 0; o >>= 1) k = acc_add(k, shfl_xor_acc2(k, o));
+  return k;
+}
+
 // Rows [w.start, w.start + w.count) of a dense instance on its FP64 or FP32
 // data (pair batches: split on every load); returns the tile's f.
 template <typename T, bool PAIR, int TEAM>
@@ -191,9 +203,7 @@ __device__ double dense_tile(const BInst& I, const BItem& w, unsigned char* wsp,
         Acc* ra = reinterpret_cast<Acc*>(red) + (itr & 1) * 2 * BW + team * 2 * TW;  // [TW][2]
         if ((lane & (W / 2 - 1)) == 0) ra[(warp % TW) * 2 + (upper ? 1 : 0)] = keep;
         team_barrier<TEAM>(team);
-        keep = ra[upper ? 1 : 0];
-#pragma unroll
-        for (int q = 1; q < TW; ++q) keep = acc_add(keep, ra[q * 2 + (upper ? 1 : 0)]);
+        keep = team_warps_sum<TW>(ra, lane, upper);
       }
       const Acc other = shfl_xor_acc2(keep, W / 2);
       const Acc yt[2] = {upper ? other : keep, upper ? keep : other};
@@ -469,9 +479,7 @@ __device__ double dense_tile_ring(const BInst& I, const BItem& w, const Ring& R,
     }
     ++g;
     if constexpr (TEAM > 32) {
-      keep = ra[upper ? 1 : 0];
-#pragma unroll
-      for (int q = 1; q < TW; ++q) keep = acc_add(keep, ra[q * 2 + (upper ? 1 : 0)]);
+      keep = team_warps_sum<TW>(ra, lane, upper);
     }
     const Acc other = shfl_xor_acc2(keep, W / 2);
     const Acc yt[2] = {upper ? other : keep, upper ? keep : other};
