@@ -855,8 +855,8 @@ _TRAFFIC = {
                        '166f724fdbe0f6dd'),
     ('tetcsr', 'f64'): (787957760, ['tet_tile.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
                         '166f724fdbe0f6dd'),
-    ('batched', 'f64'): (18506292224, ['batched.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
-                         '9aead89481d34e3c'),
+    ('batched', 'f64'): (18503473152, ['batched.cu', 'kg_tet_elem.cuh', 'kg_pair.cuh', 'kg_device.cuh'],
+                         '2bc7e7b9c7b540ad'),
 }
 
 
