@@ -92,3 +92,32 @@ def test_fp64_peak_prefers_the_measured_rate():
     assert bench.fp64_peak(peaks, {"fp64_fma_tflops": 1.19})[0] == 1.19
     assert bench.fp64_peak(peaks, {"error": "x"})[0] == 1.258
     assert bench.fp64_peak(peaks, None)[0] == 1.258
+
+
+def test_batched_profiling_case_takes_the_full_batchs_instances():
+    # batched_big: the first 96 dense instances of the 4096-instance draw with 1024 <= n < 2048,
+    # at their indices in that draw (their seeds), and no tets; the full batch keeps everything
+    from paper_2507_13204_gb300 import workloads as W
+    drawn = W.batched_dense_sizes(4096)
+    ks, sizes, boxes = bench.make_workload("batched_big", "auto").instances()
+    assert len(ks) == 96 and boxes == []
+    assert ks == [k for k, n in enumerate(drawn) if 1024 <= n < 2048][:96]
+    assert sizes == [int(drawn[k]) for k in ks]
+    ks, sizes, boxes = bench.make_workload("batched", "auto").instances()
+    assert ks == list(range(4096)) and len(boxes) == 512
+
+
+def test_sparse_random_access_record():
+    # least time = nnz / gather rate + nnz / (reduction rate, ATOMIC; gather rate, CSC)
+    wl = bench.SparseWL(1 << 10, "f64")
+    wl.nnz = 1_000_000
+    box = {"fp64_gather_gops": 300.0, "fp32_gather_gops": 310.0, "fp64_red_gops": 200.0,
+           "fp32_red_gops": 205.0}
+    rec = wl.l2_record(0.02, 0.01, "atomic", box)
+    least = 1e6 / 300e9 + 1e6 / 200e9
+    assert abs(rec["least_ms"] - round(least * 1e3, 5)) < 1e-9
+    assert rec["reverse"] == "red" and rec["accesses_per_step"] == 2_000_000
+    assert abs(rec["frac_of_step"] - round(least * 1e3 / 0.02, 4)) < 1e-9
+    rec = wl.l2_record(0.02, 0.01, "transpose", box)
+    assert rec["reverse"] == "gather" and rec["frac_of_kernel"] is None
+    assert abs(rec["least_ms"] - round(2e6 / 300e9 * 1e3, 5)) < 1e-9
