@@ -98,8 +98,13 @@ typedef enum { KG_F64 = 0, KG_F32 = 1 } kg_dtype;
  *             column of the transpose (built at kg_create) gathers
  *             xbar_j = 2 fbar sum_i a_ij y_i in ascending i; reproducible.
  *   FUSED     (dense) one pass over A: each team computes y_i, broadcasts
- *             ybar_i and accumulates ybar_i A_i,: into private partials that a
- *             second tiny kernel sums in a fixed order; reproducible.
+ *             ybar_i and accumulates ybar_i A_i,: into private partials that are
+ *             summed in a fixed order; reproducible.  The TMA-streamed kernels
+ *             (FP32, and FP64 in PAIR arithmetic with the prepared A for
+ *             2048 < n <= 10240) sum them in their own tail after a bounded
+ *             grid barrier, as one cooperative launch; the others (and these
+ *             when the grid cannot be resident at once) in a second small
+ *             kernel, with the same bits.
  *   SHARED    (tet) the forward schedule with the scatter-adds of each tile of
  *             elements first combined per vertex in a shared-memory table, then
  *             one global atomic per distinct vertex (Sec. 5: shared memory for
